@@ -1,0 +1,270 @@
+/*
+ * sptrsv.h -- C ABI of the GB300 (sm_103a) sparse triangular solver.
+ *
+ * Solves the sparse triangular systems of Li, "On Parallel Solution of Sparse
+ * Triangular Linear Systems in CUDA" (arXiv:1710.04985), eq. (1):
+ *
+ *      (L + D) x = f      or      (U + D) x = f,
+ *
+ * with the matrix in CSR (Sec. 3).  A setup phase (Sec. 4.4) validates the
+ * pattern and computes the level of every unknown and the level sets
+ * (Sec. 4.1); a solve phase then runs either the level-scheduled solve
+ * (Alg. 1, one launch per level) or the self-scheduled solve (Alg. 3, one
+ * launch, each row starting as soon as its dependencies are published).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - The matrix is square, n x n, CSR: rowptr int32[n+1], colidx int32[nnz],
+ *    vals float64 or float32 [nnz], 0-based, column indices strictly
+ *    increasing within a row, every entry in the declared triangle.  Unlike
+ *    Sec. 3 (which keeps D apart in a vector d) the diagonal is stored in its
+ *    row: the last entry of a lower row, the first entry of an upper row.
+ *    With SPTRSV_UNIT the diagonal is taken to be 1 and a stored diagonal
+ *    entry, if present, is ignored.
+ *  - All array arguments named d_* are DEVICE pointers on the device that
+ *    was current when the plan was made.  Sizes are element counts.
+ *  - Right-hand sides and solutions are row-major [n][ld] with nrhs <= ld
+ *    columns in use (a torch (n, nrhs) tensor has ld = nrhs).  d_x == d_b
+ *    (an in-place solve, as in Sec. 3.1 where x starts as f) is allowed.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Every
+ *    solve is enqueued on it and returns without synchronising.
+ *  - Nothing throws across the ABI; every call returns a status.
+ *
+ * Ownership
+ * ---------
+ *  The caller owns every array it passes.  The plan BORROWS d_rowptr,
+ *  d_colidx and d_vals: they must stay valid, with the same pattern, until
+ *  sptrsv_free.  Values may change between solves without re-analysis (the
+ *  ILU refactorisation case of Sec. 1).  The plan OWNS its level arrays, the
+ *  transposed pattern, its counters, its status word and its scratch.
+ *  Solves on one plan must be serialised (one stream at a time): they share
+ *  the plan's counters and scratch.
+ *
+ * Errors
+ * ------
+ *  Structural errors are found by sptrsv_analyze, which synchronises its
+ *  stream once.  Device-side failures of a solve (a dependency wait that ran
+ *  past its limit) are recorded in the plan's status word and returned by
+ *  sptrsv_status.
+ */
+#ifndef SPTRSV_H
+#define SPTRSV_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define SPTRSV_API __attribute__((visibility("default")))
+#else
+#define SPTRSV_API
+#endif
+
+typedef struct sptrsv_plan_s *sptrsv_plan_t;
+
+typedef enum {
+    SPTRSV_OK = 0,
+    SPTRSV_ERR_INVALID_ARG = 1,   /* bad size, null pointer, bad enum, ld < nrhs, ...   */
+    SPTRSV_ERR_STRUCTURE = 2,     /* unsorted/duplicate column, entry outside triangle,
+                                     column out of range, bad rowptr                     */
+    SPTRSV_ERR_ZERO_PIVOT = 3,    /* missing or zero diagonal (Sec. 3 assumes none)      */
+    SPTRSV_ERR_CUDA = 4,          /* a CUDA runtime call failed                          */
+    SPTRSV_ERR_OOM = 5,           /* device allocation failed                            */
+    SPTRSV_ERR_TIMEOUT = 6,       /* a dependency wait ran past the spin limit           */
+    SPTRSV_ERR_NOT_SUPPORTED = 7, /* e.g. a call that must allocate while capturing      */
+    SPTRSV_ERR_INTERNAL = 8       /* a self-check of the setup failed (a library bug);
+                                     the plan is not created                             */
+} sptrsv_status_t;
+
+typedef enum { SPTRSV_F64 = 0, SPTRSV_F32 = 1 } sptrsv_dtype_t;
+typedef enum { SPTRSV_LOWER = 0, SPTRSV_UPPER = 1 } sptrsv_uplo_t;
+typedef enum { SPTRSV_NON_UNIT = 0, SPTRSV_UNIT = 1 } sptrsv_diag_t;
+typedef enum {
+    SPTRSV_ALGO_LEVEL = 0,        /* Alg. 1 (LEVR): one launch per level                 */
+    SPTRSV_ALGO_SELF = 1          /* Alg. 3 (SLFR): one launch, rows self-scheduled      */
+} sptrsv_algo_t;
+
+/* ------------------------------------------------------------------ setup */
+
+/* Setup phase (Sec. 4.4, Table 1): validates the CSR (Sec. 3), computes the
+ * 0-based level of every row, lev(i) = 1 + max lev(j) over the off-diagonal
+ * entries j of row i (Sec. 4.1; roots get 0), and the level sets
+ * (nlev, ilev[nlev+1], jlev[n]) with rows in ascending index order inside a
+ * level.  An upper triangle is swept in reverse (Sec. 4.1).
+ *   n, nnz        matrix order and stored entries (0 <= n, 0 <= nnz < 2^31)
+ *   d_rowptr ...  device CSR, borrowed until sptrsv_free (see above)
+ *   dtype         element type of d_vals
+ *   uplo, diag    triangle and diagonal kind
+ *   stream        the setup runs on it and synchronises it once
+ *   plan          out: the new plan, or NULL on error
+ * Returns SPTRSV_ERR_STRUCTURE / SPTRSV_ERR_ZERO_PIVOT for an invalid matrix;
+ * sptrsv_last_error_row() then gives the first offending row. */
+SPTRSV_API sptrsv_status_t sptrsv_analyze(int n, int nnz, const int *d_rowptr,
+                               const int *d_colidx, const void *d_vals,
+                               sptrsv_dtype_t dtype, sptrsv_uplo_t uplo,
+                               sptrsv_diag_t diag, void *stream,
+                               sptrsv_plan_t *plan);
+
+/* Releases everything the plan owns (synchronises the device first). */
+SPTRSV_API sptrsv_status_t sptrsv_free(sptrsv_plan_t plan);
+
+/* ------------------------------------------------------------------ solve */
+
+/* Solves op(A) x = b with op = identity: forward substitution for a lower
+ * plan, backward for an upper one (Sec. 3.1), by Alg. 1 (SPTRSV_ALGO_LEVEL)
+ * or Alg. 3 (SPTRSV_ALGO_SELF).
+ *   d_b, d_x  device [n][ld], element type of the plan, nrhs >= 1 columns
+ *   ld        leading dimension of both, ld >= nrhs
+ * With SPTRSV_ALGO_SELF, x is overwritten with a "not yet solved" marker
+ * before the solve kernel runs, so x must not alias anything else the solve
+ * reads except b itself (x == b is handled with plan scratch).
+ * Asynchronous; device-side failures go to sptrsv_status.  Graph capturable
+ * (an in-place SELF solve allocates its scratch on first use: make that
+ * first call outside capture). */
+SPTRSV_API sptrsv_status_t sptrsv_solve(sptrsv_plan_t plan, const void *d_b, void *d_x,
+                             int nrhs, int ld, sptrsv_algo_t algo,
+                             void *stream);
+
+/* Solves A^T y = g (the adjoint solve used by the backward pass).  Sec. 3.2
+ * reads a CSR matrix as the CSC of its transpose; the plan builds the CSR of
+ * A^T (pattern plus a map into d_vals, so values are never copied) and its
+ * levels, swept in the opposite direction (Sec. 4.1), on first use.  That
+ * first call synchronises `stream` and allocates: make it outside capture.
+ * Arguments as for sptrsv_solve. */
+SPTRSV_API sptrsv_status_t sptrsv_solve_transpose(sptrsv_plan_t plan, const void *d_b,
+                                       void *d_x, int nrhs, int ld,
+                                       sptrsv_algo_t algo, void *stream);
+
+/* Builds the transposed pattern and its levels now (see
+ * sptrsv_solve_transpose); synchronises `stream`. */
+SPTRSV_API sptrsv_status_t sptrsv_prepare_transpose(sptrsv_plan_t plan, void *stream);
+
+/* ------------------------------------------------------- differentiation */
+
+/* Gradient of a loss through x = A^{-1} b with respect to the stored values:
+ * from eq. (1), dx = -A^{-1} (dA) x, so for every stored (i, j)
+ *     d_gvals[p] = - sum_c d_y[i][c] * d_x[j][c]
+ * where y = A^{-T} (dloss/dx) comes from sptrsv_solve_transpose.  Entries on
+ * the diagonal of a SPTRSV_UNIT plan get 0.  d_y, d_x: [n][ld] device arrays
+ * of the plan's type; d_gvals: [nnz] device array of the plan's type, on the
+ * plan's pattern.  Asynchronous. */
+SPTRSV_API sptrsv_status_t sptrsv_grad_vals(sptrsv_plan_t plan, const void *d_y,
+                                 const void *d_x, int nrhs, int ld,
+                                 void *d_gvals, void *stream);
+
+/* --------------------------------------------------------------- precision */
+
+/* FP64 residual r = b - A x of system (1) (diagonal taken as 1 for a unit
+ * plan).  F64 plans only.  All three arrays [n][ld], device.  Asynchronous. */
+SPTRSV_API sptrsv_status_t sptrsv_residual(sptrsv_plan_t plan, const double *d_b,
+                                const double *d_x, double *d_r, int nrhs,
+                                int ld, void *stream);
+
+/* Mixed-precision solve with iterative refinement (F64 plans only; the
+ * motivation is the refinement use of Sec. 1).  The bulk triangular solves
+ * run in FP32 (an FP32 copy of the values, FP32 vectors and accumulation);
+ * the residual r = b - A x, the correction update x += d and the solution
+ * are FP64.  Stops when max|r| / (max|b| + ||A||_inf max|x|) <= tol or after
+ * max_iter corrections.
+ *   d_b, d_x     device FP64 [n][ld]; x is overwritten (no initial guess)
+ *   iters        out (nullable): corrections applied after the first solve
+ *   rel_resid    out (nullable): the last relative residual measured
+ * Synchronises `stream` once per iteration to read the residual norm; the
+ * first call allocates the FP32 copy and scratch.  Not graph capturable.
+ * Refresh the FP32 copy after changing the values with
+ * sptrsv_refresh_values. */
+SPTRSV_API sptrsv_status_t sptrsv_solve_refined(sptrsv_plan_t plan, const double *d_b,
+                                     double *d_x, int nrhs, int ld,
+                                     int max_iter, double tol, int *iters,
+                                     double *rel_resid, void *stream);
+
+/* Points the plan at a new values array with the same pattern and element
+ * type (for example a new parameter tensor); borrowed like the first one.
+ * The FP32 copy, if any, is refreshed on `stream`.  The diagonal is not
+ * re-checked: it must stay nonzero.  Asynchronous. */
+SPTRSV_API sptrsv_status_t sptrsv_set_values(sptrsv_plan_t plan, const void *d_vals,
+                                             void *stream);
+
+/* Re-reads d_vals into the plan's FP32 copy (if one exists).  Async. */
+SPTRSV_API sptrsv_status_t sptrsv_refresh_values(sptrsv_plan_t plan, void *stream);
+
+/* ----------------------------------------------------------------- tuning */
+
+/* Launch shape of the solve kernels.  lanes_per_row in {1,2,4,8,16,32}: a
+ * row is reduced by a sub-warp of that many lanes, so one warp holds
+ * 32 / lanes_per_row rows; block_size a multiple of 32 in [32, 1024];
+ * max_blocks caps the persistent grid of the self-scheduled solve (0 = as
+ * many as fit on the device at once).  Applies to the forward and the
+ * transposed solves.  Multi-RHS solves pick their own width from nrhs. */
+SPTRSV_API sptrsv_status_t sptrsv_set_tuning(sptrsv_plan_t plan, int lanes_per_row,
+                                  int block_size, int max_blocks);
+SPTRSV_API sptrsv_status_t sptrsv_get_tuning(sptrsv_plan_t plan, int *lanes_per_row,
+                                  int *block_size, int *max_blocks);
+
+/* Upper bound on the polls of one dependency wait before the wait gives up,
+ * records SPTRSV_ERR_TIMEOUT with its row and publishes NaN so that every
+ * later row still finishes.  Default 2^24 (several seconds with the
+ * built-in back-off); the environment variable SPTRSV_SPIN_LIMIT overrides
+ * the default for new plans. */
+SPTRSV_API sptrsv_status_t sptrsv_set_spin_limit(sptrsv_plan_t plan, long long polls);
+
+/* -------------------------------------------------------------- inspection */
+
+/* Level data of the forward (transpose = 0) or transposed (transpose = 1)
+ * system: nlev, and device pointers (owned by the plan) to lev[n],
+ * ilev[nlev+1] and jlev[n].  The transposed data exist only after
+ * sptrsv_prepare_transpose or a transposed solve. */
+SPTRSV_API sptrsv_status_t sptrsv_levels(sptrsv_plan_t plan, int transpose, int *nlev,
+                              const int **d_lev, const int **d_ilev,
+                              const int **d_jlev);
+
+/* Transposed pattern (CSR of A^T): tptr[n+1], tidx[nnz] and tmap[nnz], with
+ * (A^T) entry q equal to d_vals[tmap[q]]. */
+SPTRSV_API sptrsv_status_t sptrsv_transpose_pattern(sptrsv_plan_t plan,
+                                         const int **d_tptr,
+                                         const int **d_tidx,
+                                         const int **d_tmap);
+
+/* Synchronises `stream`, then returns and clears the first device-side
+ * failure recorded since the last call (SPTRSV_OK if none); *error_row
+ * (nullable) receives its row, or -1. */
+SPTRSV_API sptrsv_status_t sptrsv_status(sptrsv_plan_t plan, void *stream,
+                              int *error_row);
+
+/* Row of the last STRUCTURE / ZERO_PIVOT error of sptrsv_analyze on this
+ * host thread, or -1. */
+SPTRSV_API int sptrsv_last_error_row(void);
+
+/* Human-readable name of a status, and the text of the last CUDA error seen
+ * on this host thread. */
+SPTRSV_API const char *sptrsv_status_string(sptrsv_status_t status);
+SPTRSV_API const char *sptrsv_last_cuda_error(void);
+
+/* Wall time of the last sptrsv_analyze of this plan (ms, host clock around
+ * the synchronised setup). */
+SPTRSV_API sptrsv_status_t sptrsv_analysis_ms(sptrsv_plan_t plan, double *ms);
+
+/* Kernel timing.  While enabled, every solve records a pair of CUDA events
+ * around its main kernel work (for the self-scheduled solve: the solve
+ * kernel alone; for the level-scheduled solve: the whole per-level launch
+ * sequence) on the solve's stream.  sptrsv_profile_read synchronises those
+ * events and returns the summed milliseconds and the number of solves timed
+ * since the last read, then clears them.  Not for use under graph capture. */
+SPTRSV_API sptrsv_status_t sptrsv_profile_enable(sptrsv_plan_t plan, int enable);
+SPTRSV_API sptrsv_status_t sptrsv_profile_read(sptrsv_plan_t plan, double *total_ms,
+                                    int *count);
+
+/* Kernels enqueued by the last solve call on this plan (for launch
+ * accounting). */
+SPTRSV_API int sptrsv_last_launch_count(sptrsv_plan_t plan);
+
+/* Test hook: the self-scheduled solve skips publishing this row (-1 = off),
+ * so that every row depending on it exercises the bounded wait and the
+ * SPTRSV_ERR_TIMEOUT path.  Faults nothing: the waits end at the limit. */
+SPTRSV_API sptrsv_status_t sptrsv_debug_withhold_row(sptrsv_plan_t plan, int row);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPTRSV_H */

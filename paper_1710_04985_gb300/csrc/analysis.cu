@@ -1,0 +1,419 @@
+// Setup phase (Sec. 4.4): validation, level analysis (Sec. 4.1), level sets,
+// and the CSR of the transpose (the CSC view of Sec. 3.2).
+//
+// Level analysis here is not Kahn's algorithm (Sec. 4.4.1, one launch and
+// one device-to-host copy per level).  It is one persistent launch that
+// sweeps the rows in substitution order: lev(i) = 1 + max lev(j) is itself a
+// triangular "solve" in the (max, +) semiring, so each row waits for its
+// dependencies' levels exactly as the self-scheduled solve waits for their
+// values, and publishes its own level as soon as it is known.
+#include "internal.h"
+
+namespace sptrsv {
+
+// ------------------------------------------------------------ validation
+// One thread per row.  Checks (Sec. 3): rowptr monotone inside [0, nnz];
+// columns in range, strictly increasing, inside the declared triangle;
+// unless unit, a nonzero diagonal in its place (last entry of a lower row,
+// first of an upper row).
+__global__ void validate_k(int n, int nnz, const int* __restrict__ ptr,
+                           const int* __restrict__ idx, const void* __restrict__ vals, int f64,
+                           int upper, int unit, unsigned long long* status) {
+    for (long long ii = (long long)blockIdx.x * blockDim.x + threadIdx.x; ii < n;
+         ii += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)ii;
+        const int beg = ptr[i], end = ptr[i + 1];
+        if ((i == 0 && beg != 0) || (i == n - 1 && end != nnz) || beg < 0 || beg > end ||
+            end > nnz) {
+            report(status, i, kCodeStructure);
+            continue;
+        }
+        int prev = -1;
+        bool bad = false;
+        for (int q = beg; q < end; ++q) {
+            const int c = idx[q];
+            if (c <= prev || c >= n || (upper ? c < i : c > i)) {
+                bad = true;
+                break;
+            }
+            prev = c;
+        }
+        if (bad) {
+            report(status, i, kCodeStructure);
+            continue;
+        }
+        if (!unit) {
+            const int q = upper ? beg : end - 1;
+            if (end == beg || idx[q] != i) {
+                report(status, i, kCodeZeroPivot);
+                continue;
+            }
+            const double v = f64 ? ((const double*)vals)[q] : (double)((const float*)vals)[q];
+            if (v == 0.0) report(status, i, kCodeZeroPivot);
+        }
+    }
+}
+
+cudaError_t launch_validate(int n, int nnz, const int* ptr, const int* idx, const void* vals,
+                            bool f64, bool upper, bool unit, unsigned long long* status,
+                            int grid, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    int g = (n + 255) / 256;
+    if (g > grid) g = grid;
+    validate_k<<<g, 256, 0, s>>>(n, nnz, ptr, idx, vals, f64, upper, unit, status);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ level sweep
+// Sub-warps of W lanes take groups of 32/W consecutive rows (in substitution
+// order) from a ticket counter.  Every dependency of a row comes earlier in
+// that order, and every earlier ticket is held by a running warp, so the
+// sweep cannot deadlock whatever the residency.  lev[] starts at -1
+// ("unknown"); a row publishes its level with one relaxed store.
+template <int W>
+__global__ void level_sweep_k(int n, const int* __restrict__ ptr, const int* __restrict__ idx,
+                              int upper, int* lev, int* ticket, int* nlev,
+                              unsigned long long* status, SpinPolicy sp) {
+    constexpr int R = 32 / W;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane / W;
+    const int sl = lane - sub * W;
+    const unsigned gmask = group_mask<W>(lane);
+    int local_max = -1;
+    int t = 0;
+    if (lane == 0) t = atomicAdd(ticket, 1);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    while ((long long)t * R < n) {
+        int tn = 0;
+        if (lane == 0) tn = atomicAdd(ticket, 1);
+        const long long q = (long long)t * R + sub;
+        if (q < n) {
+            const int i = upper ? n - 1 - (int)q : (int)q;
+            const int beg = ptr[i], end = ptr[i + 1];
+            int m = -1;
+            for (int e = beg + sl; e < end; e += W) {
+                const int c = idx[e];
+                if (c != i) m = max(m, wait_level(lev + c, sp, status, i));
+            }
+            m = group_max<W>(m, gmask);
+            if (sl == 0) {
+                st_relaxed(lev + i, m + 1);
+                local_max = max(local_max, m + 1);
+            }
+        }
+        t = __shfl_sync(0xffffffffu, tn, 0);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+        local_max = max(local_max, __shfl_xor_sync(0xffffffffu, local_max, off));
+    if (lane == 0 && local_max >= 0) atomicMax(nlev, local_max + 1);
+}
+
+template <int W>
+static cudaError_t sweep_w(int n, const int* ptr, const int* idx, bool upper, int* lev,
+                           int* ticket, int* nlev, unsigned long long* status, SpinPolicy sp,
+                           int grid, int block, cudaStream_t s) {
+    level_sweep_k<W><<<grid, block, 0, s>>>(n, ptr, idx, upper, lev, ticket, nlev, status, sp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_level_sweep(int lanes, int n, const int* ptr, const int* idx, bool upper,
+                               int* lev, int* ticket, int* nlev, unsigned long long* status,
+                               SpinPolicy sp, int grid, int block, cudaStream_t s) {
+    switch (lanes) {
+        case 1: return sweep_w<1>(n, ptr, idx, upper, lev, ticket, nlev, status, sp, grid, block, s);
+        case 2: return sweep_w<2>(n, ptr, idx, upper, lev, ticket, nlev, status, sp, grid, block, s);
+        case 4: return sweep_w<4>(n, ptr, idx, upper, lev, ticket, nlev, status, sp, grid, block, s);
+        case 8: return sweep_w<8>(n, ptr, idx, upper, lev, ticket, nlev, status, sp, grid, block, s);
+        case 16: return sweep_w<16>(n, ptr, idx, upper, lev, ticket, nlev, status, sp, grid, block, s);
+        case 32: return sweep_w<32>(n, ptr, idx, upper, lev, ticket, nlev, status, sp, grid, block, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int level_sweep_blocks_per_sm(int lanes, int block) {
+    int nb = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (lanes) {
+        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, level_sweep_k<1>, block, 0); break;
+        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, level_sweep_k<2>, block, 0); break;
+        case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, level_sweep_k<4>, block, 0); break;
+        case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, level_sweep_k<8>, block, 0); break;
+        case 16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, level_sweep_k<16>, block, 0); break;
+        case 32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, level_sweep_k<32>, block, 0); break;
+    }
+    return (e == cudaSuccess && nb > 0) ? nb : 1;
+}
+
+// ------------------------------------------------------------ histogram
+// count[keys[e]] += 1, with lanes holding equal keys combined first.
+__global__ void histogram_k(const int* __restrict__ keys, int m, int* count, int bins,
+                            unsigned long long* status) {
+    for (long long e0 = (long long)blockIdx.x * blockDim.x; e0 < m;
+         e0 += (long long)gridDim.x * blockDim.x) {
+        const long long e = e0 + threadIdx.x;
+        const int lane = threadIdx.x & 31;
+        int key = e < m ? keys[e] : -1 - lane;  // invalid lanes never match
+        if (e < m && (key < 0 || key >= bins)) {
+            report(status, (int)e, kCodeInternal);
+            key = -1 - lane;
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd(count + key, __popc(peers));
+    }
+}
+
+cudaError_t launch_histogram(const int* keys, int m, int* count, int bins,
+                             unsigned long long* status, cudaStream_t s) {
+    if (m == 0) return cudaSuccess;
+    long long g = ((long long)m + 255) / 256;
+    if (g > 4096) g = 4096;
+    histogram_k<<<(int)g, 256, 0, s>>>(keys, m, count, bins, status);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ exclusive scan
+// One block of 1024 threads; thread t owns a contiguous chunk of the input.
+__global__ void __launch_bounds__(1024) exclusive_scan_k(const int* __restrict__ in, int* out,
+                                                         int m) {
+    __shared__ int warp_tot[32];
+    const int per = (m + 1023) / 1024;
+    const long long lo = (long long)threadIdx.x * per;
+    const long long hi = lo + per < m ? lo + per : m;
+    int s = 0;
+    for (long long e = lo; e < hi; ++e) s += in[e];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int incl = s;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
+    }
+    if (lane == 31) warp_tot[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        const int v = warp_tot[lane];
+        int wi = v;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, wi, off);
+            if (lane >= off) wi += y;
+        }
+        warp_tot[lane] = wi - v;
+    }
+    __syncthreads();
+    int run = warp_tot[w] + incl - s;
+    for (long long e = lo; e < hi; ++e) {
+        const int v = in[e];
+        out[e] = run;
+        run += v;
+    }
+    if (threadIdx.x == 1023) out[m] = run;
+}
+
+cudaError_t launch_exclusive_scan(const int* in, int* out, int m, cudaStream_t s) {
+    exclusive_scan_k<<<1, 1024, 0, s>>>(in, out, m);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ radix sort
+// Stable LSD radix sort, 8-bit digits.  Per pass: per-tile digit counts,
+// one exclusive scan over (digit, tile), then a stable scatter in which
+// each warp ranks its lanes with __match_any_sync and warps are ordered
+// through a shared-memory table.
+constexpr int kRsThreads = 512;
+constexpr int kRsTile = 8192;
+constexpr int kRsWarps = kRsThreads / 32;
+
+int radix_hist_entries(int m) {
+    const int nb = (m + kRsTile - 1) / kRsTile;
+    return 256 * (nb > 0 ? nb : 1);
+}
+
+__global__ void __launch_bounds__(kRsThreads) rs_hist_k(const int* __restrict__ keys, int m,
+                                                        int shift, int* ghist, int nb) {
+    __shared__ int h[256];
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) h[t] = 0;
+    __syncthreads();
+    const long long t0 = (long long)blockIdx.x * kRsTile;
+    const long long t1 = t0 + kRsTile < m ? t0 + kRsTile : m;
+    for (long long e = t0 + threadIdx.x; e < t1; e += blockDim.x)
+        atomicAdd(&h[(keys[e] >> shift) & 255], 1);
+    __syncthreads();
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) ghist[t * nb + blockIdx.x] = h[t];
+}
+
+__global__ void __launch_bounds__(kRsThreads) rs_scatter_k(const int* __restrict__ kin,
+                                                           const int* __restrict__ vin, int m,
+                                                           int shift, const int* __restrict__ gofs,
+                                                           int nb, int* kout, int* vout,
+                                                           unsigned long long* status) {
+    __shared__ int table[kRsWarps][256];
+    __shared__ int base[256];
+    __shared__ int total[256];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int t = threadIdx.x; t < 256; t += kRsThreads) base[t] = gofs[t * nb + blockIdx.x];
+    const long long t0 = (long long)blockIdx.x * kRsTile;
+    const long long t1 = t0 + kRsTile < m ? t0 + kRsTile : m;
+    for (long long c0 = t0; c0 < t1; c0 += kRsThreads) {
+        for (int t = threadIdx.x; t < kRsWarps * 256; t += kRsThreads) (&table[0][0])[t] = 0;
+        __syncthreads();
+        const long long e = c0 + threadIdx.x;
+        const bool valid = e < t1;
+        int key = 0, val = 0, d = 256 + lane;  // invalid lanes: a digit nobody else has
+        if (valid) {
+            key = kin[e];
+            val = vin ? vin[e] : (int)e;
+            d = (key >> shift) & 255;
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        if (valid && lane == __ffs(peers) - 1) table[w][d] = __popc(peers);
+        __syncthreads();
+        if (threadIdx.x < 256) {
+            int run = 0;
+            for (int ww = 0; ww < kRsWarps; ++ww) {
+                const int c = table[ww][threadIdx.x];
+                table[ww][threadIdx.x] = run;
+                run += c;
+            }
+            total[threadIdx.x] = run;
+        }
+        __syncthreads();
+        if (valid) {
+            const int pos = base[d] + table[w][d] + rank;
+            if (pos >= 0 && pos < m) {
+                kout[pos] = key;
+                vout[pos] = val;
+            } else {
+                report(status, (int)e, kCodeInternal);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < 256) base[threadIdx.x] += total[threadIdx.x];
+    }
+}
+
+__global__ void iota_k(int* out, int m) {
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (long long)gridDim.x * blockDim.x)
+        out[e] = (int)e;
+}
+
+cudaError_t launch_iota(int* out, int m, cudaStream_t s) {
+    if (m == 0) return cudaSuccess;
+    long long g = ((long long)m + 255) / 256;
+    if (g > 4096) g = 4096;
+    iota_k<<<(int)g, 256, 0, s>>>(out, m);
+    return cudaGetLastError();
+}
+
+cudaError_t radix_sort_values(const int* keys_in, const int* vals_in, int m, int bits,
+                              int* vals_out, int* k_a, int* v_a, int* k_b, int* v_b, int* hist,
+                              int* hist_scan, unsigned long long* status, cudaStream_t s) {
+    if (m == 0) return cudaSuccess;
+    const int passes = (bits + 7) / 8;
+    if (passes == 0) {
+        if (vals_in) return cudaMemcpyAsync(vals_out, vals_in, sizeof(int) * (size_t)m,
+                                            cudaMemcpyDeviceToDevice, s);
+        return launch_iota(vals_out, m, s);
+    }
+    const int nb = (m + kRsTile - 1) / kRsTile;
+    const int* kin = keys_in;
+    const int* vin = vals_in;
+    for (int pass = 0; pass < passes; ++pass) {
+        const int shift = 8 * pass;
+        int* kout = (pass & 1) ? k_b : k_a;
+        int* vout = (pass == passes - 1) ? vals_out : ((pass & 1) ? v_b : v_a);
+        rs_hist_k<<<nb, kRsThreads, 0, s>>>(kin, m, shift, hist, nb);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        e = launch_exclusive_scan(hist, hist_scan, 256 * nb, s);
+        if (e != cudaSuccess) return e;
+        rs_scatter_k<<<nb, kRsThreads, 0, s>>>(kin, vin, m, shift, hist_scan, nb, kout, vout,
+                                                 status);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        kin = kout;
+        vin = vout;
+    }
+    return cudaSuccess;
+}
+
+// ------------------------------------------------------------ transpose helpers
+__global__ void row_of_entries_k(int n, const int* __restrict__ ptr, int* rowof) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int end = ptr[i + 1];
+        for (int q = ptr[i]; q < end; ++q) rowof[q] = (int)i;
+    }
+}
+
+cudaError_t launch_row_of_entries(int n, const int* ptr, int* rowof, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    long long g = ((long long)n + 255) / 256;
+    if (g > 4096) g = 4096;
+    row_of_entries_k<<<(int)g, 256, 0, s>>>(n, ptr, rowof);
+    return cudaGetLastError();
+}
+
+__global__ void gather_k(const int* __restrict__ src, int src_len,
+                         const int* __restrict__ index, int m, int* out,
+                         unsigned long long* status) {
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int j = index[e];
+        if (j >= 0 && j < src_len) {
+            out[e] = src[j];
+        } else {
+            out[e] = -1;
+            report(status, (int)e, kCodeInternal);
+        }
+    }
+}
+
+cudaError_t launch_gather(const int* src, int src_len, const int* index, int m, int* out,
+                          unsigned long long* status, cudaStream_t s) {
+    if (m == 0) return cudaSuccess;
+    long long g = ((long long)m + 255) / 256;
+    if (g > 8192) g = 8192;
+    gather_k<<<(int)g, 256, 0, s>>>(src, src_len, index, m, out, status);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ level-set check
+__global__ void verify_levels_k(int n, int nlev, const int* __restrict__ lev,
+                                const int* __restrict__ ilev, const int* __restrict__ jlev,
+                                unsigned long long* status) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (ilev[0] != 0 || ilev[nlev] != n))
+        report(status, 0, kCodeInternal);
+    for (long long kk = (long long)blockIdx.x * blockDim.x + threadIdx.x; kk < n;
+         kk += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)kk;
+        const int i = jlev[k];
+        if (i < 0 || i >= n) {
+            report(status, k, kCodeInternal);
+            continue;
+        }
+        const int m = lev[i];
+        if (m < 0 || m >= nlev || k < ilev[m] || k >= ilev[m + 1]) {
+            report(status, k, kCodeInternal);
+            continue;
+        }
+        if (k > ilev[m]) {
+            const int prev = jlev[k - 1];
+            if (prev >= i) report(status, k, kCodeInternal);
+        }
+    }
+}
+
+cudaError_t launch_verify_levels(int n, int nlev, const int* lev, const int* ilev,
+                                 const int* jlev, unsigned long long* status, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    long long g = ((long long)n + 255) / 256;
+    if (g > 4096) g = 4096;
+    verify_levels_k<<<(int)g, 256, 0, s>>>(n, nlev, lev, ilev, jlev, status);
+    return cudaGetLastError();
+}
+
+}  // namespace sptrsv

@@ -1,0 +1,705 @@
+// C ABI of the solver (declared in include/sptrsv.h): argument checking,
+// plan ownership, the setup sequence of Sec. 4.4 and the launch sequences of
+// the solves.  All arithmetic runs in the kernels of the other files.
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+#include "sptrsv.h"
+
+using namespace sptrsv;
+
+namespace {
+
+thread_local int g_last_error_row = -1;
+thread_local char g_last_cuda[256] = "";
+
+sptrsv_status_t cuda_fail(cudaError_t e) {
+    snprintf(g_last_cuda, sizeof(g_last_cuda), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? SPTRSV_ERR_OOM : SPTRSV_ERR_CUDA;
+}
+
+#define CK(expr)                                   \
+    do {                                           \
+        cudaError_t _e = (expr);                   \
+        if (_e != cudaSuccess) return cuda_fail(_e); \
+    } while (0)
+
+#define ST(expr)                                \
+    do {                                        \
+        sptrsv_status_t _s = (expr);            \
+        if (_s != SPTRSV_OK) return _s;         \
+    } while (0)
+
+struct Levels {
+    int nlev = 0;
+    int* lev = nullptr;
+    int* ilev = nullptr;
+    int* jlev = nullptr;
+    std::vector<int> h_ilev;
+};
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int pow2_at_least(double v) {
+    int w = 1;
+    while (w < v && w < 32) w <<= 1;
+    return w;
+}
+
+// Default sub-warp width: enough lanes for the average number of
+// off-diagonal entries of a row, at least 2, at most 32.
+int default_lanes(int n, int nnz) {
+    if (n <= 0) return 4;
+    const double off = (double)nnz / n - 1.0;
+    int w = pow2_at_least(off);
+    return w < 2 ? 2 : w;
+}
+
+// Sub-warp width of the multi-RHS kernels: one lane per column up to 32.
+int mrhs_lanes(int nrhs) {
+    int w = pow2_at_least(nrhs);
+    return w < 4 ? 4 : w;
+}
+
+bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &st) != cudaSuccess) return false;
+    return st != cudaStreamCaptureStatusNone;
+}
+
+int bits_for(int max_key) {
+    int b = 0;
+    while (b < 31 && (max_key >> b) != 0) ++b;
+    return b;
+}
+
+long long env_ll(const char* name, long long dflt) {
+    const char* v = getenv(name);
+    if (!v || !*v) return dflt;
+    char* end = nullptr;
+    long long x = strtoll(v, &end, 0);
+    return (end && *end == 0 && x > 0) ? x : dflt;
+}
+
+}  // namespace
+
+struct sptrsv_plan_s {
+    int device = 0;
+    int num_sms = 1;
+    int n = 0, nnz = 0;
+    bool f64 = true, upper = false, unit = false;
+    const int* rowptr = nullptr;
+    const int* colidx = nullptr;
+    const void* vals = nullptr;
+    Levels fwd, trn;
+    bool has_trans = false;
+    int* tptr = nullptr;
+    int* tidx = nullptr;
+    int* tmap = nullptr;
+    int* counters = nullptr;  // [0] ticket, [1] level count
+    unsigned long long* status = nullptr;
+    void* bcopy = nullptr;
+    size_t bcopy_bytes = 0;
+    float* vals32 = nullptr;
+    float* r32 = nullptr;
+    float* d32 = nullptr;
+    size_t rd_elems = 0;
+    unsigned long long* stats = nullptr;  // [0] max|r| [1] |A|_inf [2] max|x| [3] max|b|
+    int lanes = 4, block = 256, max_blocks = 0;
+    SpinPolicy spin{1ll << 24, 16, 256};
+    int withhold = -1;
+    double analysis_ms = 0.0;
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;  // start/stop pairs
+    size_t ev_used = 0;
+    int last_launches = 0;
+};
+
+namespace {
+
+void free_levels(Levels& L) {
+    cudaFree(L.lev);
+    cudaFree(L.ilev);
+    cudaFree(L.jlev);
+    L = Levels();
+}
+
+void destroy(sptrsv_plan_t P) {
+    if (!P) return;
+    DeviceGuard g(P->device);
+    free_levels(P->fwd);
+    free_levels(P->trn);
+    cudaFree(P->tptr);
+    cudaFree(P->tidx);
+    cudaFree(P->tmap);
+    cudaFree(P->counters);
+    cudaFree(P->status);
+    cudaFree(P->bcopy);
+    cudaFree(P->vals32);
+    cudaFree(P->r32);
+    cudaFree(P->d32);
+    cudaFree(P->stats);
+    for (cudaEvent_t e : P->ev) cudaEventDestroy(e);
+    delete P;
+}
+
+// Reads and clears the status word (synchronises s).  Returns the code and
+// stores the row.
+sptrsv_status_t take_status(sptrsv_plan_t P, cudaStream_t s, int* row) {
+    unsigned long long h = kStatusClear;
+    CK(cudaMemcpyAsync(&h, P->status, sizeof(h), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (row) *row = -1;
+    if (h == kStatusClear) return SPTRSV_OK;
+    CK(cudaMemsetAsync(P->status, 0xff, sizeof(unsigned long long), s));
+    CK(cudaStreamSynchronize(s));
+    if (row) *row = (int)(h >> 32);
+    return (sptrsv_status_t)(unsigned)(h & 0xffffffffu);
+}
+
+// Level analysis of one pattern (Sec. 4.1): the level sweep, then the
+// bucket sort into level sets.  Synchronises s.
+sptrsv_status_t build_levels(sptrsv_plan_t P, const int* ptr, const int* idx, bool upper,
+                             Levels& L, cudaStream_t s) {
+    const int n = P->n;
+    CK(cudaMalloc(&L.lev, sizeof(int) * (size_t)n));
+    CK(cudaMemsetAsync(L.lev, 0xff, sizeof(int) * (size_t)n, s));
+    CK(cudaMemsetAsync(P->counters, 0, 2 * sizeof(int), s));
+    const int lanes = P->lanes;
+    const int block = 256;
+    const int R = 32 / lanes;
+    const long long tickets = ((long long)n + R - 1) / R;
+    const long long want_blocks = (tickets + block / 32 - 1) / (block / 32);
+    long long grid = (long long)level_sweep_blocks_per_sm(lanes, block) * P->num_sms;
+    if (grid > want_blocks) grid = want_blocks;
+    if (grid < 1) grid = 1;
+    CK(launch_level_sweep(lanes, n, ptr, idx, upper, L.lev, P->counters, P->counters + 1,
+                          P->status, P->spin, (int)grid, block, s));
+    int nlev = 0;
+    CK(cudaMemcpyAsync(&nlev, P->counters + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+    int row = -1;
+    ST(take_status(P, s, &row));  // synchronises
+    L.nlev = nlev;
+    CK(cudaMalloc(&L.ilev, sizeof(int) * (size_t)(nlev + 1)));
+    CK(cudaMalloc(&L.jlev, sizeof(int) * (size_t)n));
+    int* count = nullptr;
+    int* scratch = nullptr;
+    const int hist_n = radix_hist_entries(n);
+    const size_t scratch_ints = (size_t)nlev + 4 * (size_t)n + 2 * (size_t)hist_n;
+    CK(cudaMalloc(&scratch, sizeof(int) * scratch_ints));
+    count = scratch;
+    int* k_a = count + nlev;
+    int* v_a = k_a + n;
+    int* k_b = v_a + n;
+    int* v_b = k_b + n;
+    int* hist = v_b + n;
+    int* hist_scan = hist + hist_n;
+    sptrsv_status_t rc = SPTRSV_OK;
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * (size_t)nlev, s);
+    if (e == cudaSuccess) e = launch_histogram(L.lev, n, count, nlev, P->status, s);
+    if (e == cudaSuccess) e = launch_exclusive_scan(count, L.ilev, nlev, s);
+    if (e == cudaSuccess)
+        e = radix_sort_values(L.lev, nullptr, n, bits_for(nlev - 1), L.jlev, k_a, v_a, k_b, v_b,
+                              hist, hist_scan, P->status, s);
+    if (e == cudaSuccess) e = launch_verify_levels(n, nlev, L.lev, L.ilev, L.jlev, P->status, s);
+    if (e == cudaSuccess) {
+        L.h_ilev.resize((size_t)nlev + 1);
+        e = cudaMemcpyAsync(L.h_ilev.data(), L.ilev, sizeof(int) * (size_t)(nlev + 1),
+                            cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = cuda_fail(e);
+    cudaFree(scratch);
+    if (rc == SPTRSV_OK) rc = take_status(P, s, &row);
+    return rc;
+}
+
+// CSR of A^T (the CSC of A, Sec. 3.2) with a value map, and its levels.
+sptrsv_status_t build_transpose(sptrsv_plan_t P, cudaStream_t s) {
+    if (P->has_trans) return SPTRSV_OK;
+    if (capturing(s)) return SPTRSV_ERR_NOT_SUPPORTED;
+    const int n = P->n, nnz = P->nnz;
+    CK(cudaMalloc(&P->tptr, sizeof(int) * (size_t)(n + 1)));
+    CK(cudaMalloc(&P->tidx, sizeof(int) * (size_t)(nnz > 0 ? nnz : 1)));
+    CK(cudaMalloc(&P->tmap, sizeof(int) * (size_t)(nnz > 0 ? nnz : 1)));
+    const int hist_n = radix_hist_entries(nnz);
+    const size_t scratch_ints = (size_t)n + 5 * (size_t)nnz + 2 * (size_t)hist_n;
+    int* scratch = nullptr;
+    CK(cudaMalloc(&scratch, sizeof(int) * scratch_ints));
+    int* count = scratch;
+    int* k_a = count + n;
+    int* v_a = k_a + nnz;
+    int* k_b = v_a + nnz;
+    int* v_b = k_b + nnz;
+    int* rowof = v_b + nnz;
+    int* hist = rowof + nnz;
+    int* hist_scan = hist + hist_n;
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * (size_t)n, s);
+    if (e == cudaSuccess) e = launch_histogram(P->colidx, nnz, count, n, P->status, s);
+    if (e == cudaSuccess) e = launch_exclusive_scan(count, P->tptr, n, s);
+    if (e == cudaSuccess)
+        e = radix_sort_values(P->colidx, nullptr, nnz, bits_for(n - 1), P->tmap, k_a, v_a, k_b,
+                              v_b, hist, hist_scan, P->status, s);
+    if (e == cudaSuccess) e = launch_row_of_entries(n, P->rowptr, rowof, s);
+    if (e == cudaSuccess) e = launch_gather(rowof, nnz, P->tmap, nnz, P->tidx, P->status, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(scratch);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int row = -1;
+    sptrsv_status_t rc = take_status(P, s, &row);
+    // The transposed pattern must itself be a valid triangle of the other
+    // kind (a self-check: any failure here is a library bug).
+    if (rc == SPTRSV_OK) {
+        CK(launch_validate(n, nnz, P->tptr, P->tidx, nullptr, P->f64, !P->upper, true, P->status,
+                           P->num_sms * 32, s));
+        rc = take_status(P, s, &row);
+    }
+    if (rc != SPTRSV_OK) return SPTRSV_ERR_INTERNAL;
+    ST(build_levels(P, P->tptr, P->tidx, !P->upper, P->trn, s));
+    P->has_trans = true;
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t ensure_bytes(void** buf, size_t* have, size_t want, cudaStream_t s) {
+    if (*have >= want) return SPTRSV_OK;
+    if (capturing(s)) return SPTRSV_ERR_NOT_SUPPORTED;
+    CK(cudaStreamSynchronize(s));
+    cudaFree(*buf);
+    *buf = nullptr;
+    *have = 0;
+    CK(cudaMalloc(buf, want));
+    *have = want;
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t prof_begin(sptrsv_plan_t P, cudaStream_t s) {
+    if (!P->prof) return SPTRSV_OK;
+    if (P->ev.size() < 2 * (P->ev_used + 1)) {
+        cudaEvent_t a, b;
+        CK(cudaEventCreate(&a));
+        CK(cudaEventCreate(&b));
+        P->ev.push_back(a);
+        P->ev.push_back(b);
+    }
+    CK(cudaEventRecord(P->ev[2 * P->ev_used], s));
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t prof_end(sptrsv_plan_t P, cudaStream_t s) {
+    if (!P->prof) return SPTRSV_OK;
+    CK(cudaEventRecord(P->ev[2 * P->ev_used + 1], s));
+    P->ev_used++;
+    return SPTRSV_OK;
+}
+
+// One triangular solve (forward pattern or transpose) of any element type:
+// `f64` selects the kernels, `vals` the values they read.
+sptrsv_status_t run_solve(sptrsv_plan_t P, bool trans, bool f64, const void* vals, const void* b,
+                          long long ldb, void* x, long long ldx, int nrhs, sptrsv_algo_t algo,
+                          cudaStream_t s) {
+    const Levels& L = trans ? P->trn : P->fwd;
+    SolveParams p;
+    memset(&p, 0, sizeof(p));
+    p.n = P->n;
+    p.ptr = trans ? P->tptr : P->rowptr;
+    p.idx = trans ? P->tidx : P->colidx;
+    p.vmap = trans ? P->tmap : nullptr;
+    p.vals = vals;
+    p.diag_first = trans ? !P->upper : P->upper;
+    p.unit = P->unit;
+    p.jlev = L.jlev;
+    p.b = b;
+    p.ldb = ldb;
+    p.x = x;
+    p.ldx = ldx;
+    p.nrhs = nrhs;
+    p.ticket = P->counters;
+    p.status = P->status;
+    p.spin = P->spin;
+    p.withhold = P->withhold;
+    const bool mrhs = nrhs > 1;
+    const int lanes = mrhs ? mrhs_lanes(nrhs) : P->lanes;
+    int launches = 0;
+    if (algo == SPTRSV_ALGO_LEVEL) {
+        ST(prof_begin(P, s));
+        for (int m = 0; m < L.nlev; ++m) {
+            p.kbeg = L.h_ilev[m];
+            p.cnt = L.h_ilev[m + 1] - L.h_ilev[m];
+            CK(mrhs ? launch_mrhs(f64, lanes, false, p, 0, P->block, s)
+                    : launch_level_k1(f64, lanes, p, P->block, s));
+        }
+        ST(prof_end(P, s));
+        launches = L.nlev;
+    } else {
+        const size_t esize = f64 ? sizeof(double) : sizeof(float);
+        void* bcopy = nullptr;
+        if (x == b) {  // in place: keep b aside, x becomes the publication buffer
+            ST(ensure_bytes(&P->bcopy, &P->bcopy_bytes, esize * (size_t)P->n * nrhs, s));
+            bcopy = P->bcopy;
+            p.b = bcopy;
+            p.ldb = nrhs;
+        }
+        CK(launch_prep_self(f64, P->n, nrhs, x, ldx, b, ldb, bcopy, P->counters,
+                            P->num_sms * 8, s));
+        const int R = 32 / lanes;
+        const long long tickets = ((long long)P->n + R - 1) / R;
+        const long long want_blocks = (tickets + P->block / 32 - 1) / (P->block / 32);
+        long long grid =
+            (long long)self_blocks_per_sm(f64, lanes, mrhs, trans, P->block) * P->num_sms;
+        if (P->max_blocks > 0 && grid > P->max_blocks) grid = P->max_blocks;
+        if (grid > want_blocks) grid = want_blocks;
+        if (grid < 1) grid = 1;
+        ST(prof_begin(P, s));
+        CK(mrhs ? launch_mrhs(f64, lanes, true, p, (int)grid, P->block, s)
+                : launch_self_k1(f64, lanes, p, (int)grid, P->block, s));
+        ST(prof_end(P, s));
+        launches = 2;
+    }
+    P->last_launches = launches;
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t solve_common(sptrsv_plan_t P, bool trans, const void* b, void* x, int nrhs,
+                             int ld, sptrsv_algo_t algo, void* stream) {
+    if (!P || nrhs < 1 || ld < nrhs || (algo != SPTRSV_ALGO_LEVEL && algo != SPTRSV_ALGO_SELF))
+        return SPTRSV_ERR_INVALID_ARG;
+    P->last_launches = 0;
+    if (P->n == 0) return SPTRSV_OK;
+    if (!b || !x) return SPTRSV_ERR_INVALID_ARG;
+    DeviceGuard g(P->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (trans) ST(build_transpose(P, s));
+    return run_solve(P, trans, P->f64, P->vals, b, ld, x, ld, nrhs, algo, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+sptrsv_status_t sptrsv_analyze(int n, int nnz, const int* d_rowptr, const int* d_colidx,
+                               const void* d_vals, sptrsv_dtype_t dtype, sptrsv_uplo_t uplo,
+                               sptrsv_diag_t diag, void* stream, sptrsv_plan_t* plan) {
+    g_last_error_row = -1;
+    if (!plan) return SPTRSV_ERR_INVALID_ARG;
+    *plan = nullptr;
+    if (n < 0 || nnz < 0 || (dtype != SPTRSV_F64 && dtype != SPTRSV_F32) ||
+        (uplo != SPTRSV_LOWER && uplo != SPTRSV_UPPER) ||
+        (diag != SPTRSV_NON_UNIT && diag != SPTRSV_UNIT))
+        return SPTRSV_ERR_INVALID_ARG;
+    if (n > 0 && (!d_rowptr || (nnz > 0 && (!d_colidx || !d_vals)))) return SPTRSV_ERR_INVALID_ARG;
+    if (n > 0 && nnz == 0 && diag == SPTRSV_NON_UNIT) {
+        g_last_error_row = 0;
+        return SPTRSV_ERR_ZERO_PIVOT;
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = (cudaStream_t)stream;
+    if (capturing(s)) return SPTRSV_ERR_NOT_SUPPORTED;
+    sptrsv_plan_t P = new sptrsv_plan_s();
+    cudaError_t e = cudaGetDevice(&P->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device);
+    if (e != cudaSuccess) {
+        destroy(P);
+        return cuda_fail(e);
+    }
+    P->n = n;
+    P->nnz = nnz;
+    P->f64 = dtype == SPTRSV_F64;
+    P->upper = uplo == SPTRSV_UPPER;
+    P->unit = diag == SPTRSV_UNIT;
+    P->rowptr = d_rowptr;
+    P->colidx = d_colidx;
+    P->vals = d_vals;
+    P->lanes = default_lanes(n, nnz);
+    P->spin.limit = env_ll("SPTRSV_SPIN_LIMIT", 1ll << 24);
+    P->spin.hot = (int)env_ll("SPTRSV_SPIN_HOT", 16);
+    P->spin.max_ns = (unsigned)env_ll("SPTRSV_SPIN_MAX_NS", 256);
+    sptrsv_status_t rc = SPTRSV_OK;
+    e = cudaMalloc(&P->counters, 4 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&P->status, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemsetAsync(P->counters, 0, 4 * sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P->status, 0xff, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) rc = cuda_fail(e);
+    if (rc == SPTRSV_OK && n > 0) {
+        e = launch_validate(n, nnz, d_rowptr, d_colidx, d_vals, P->f64, P->upper, P->unit,
+                            P->status, P->num_sms * 32, s);
+        if (e != cudaSuccess) rc = cuda_fail(e);
+        int row = -1;
+        if (rc == SPTRSV_OK) rc = take_status(P, s, &row);
+        if (rc == SPTRSV_ERR_STRUCTURE || rc == SPTRSV_ERR_ZERO_PIVOT) g_last_error_row = row;
+        if (rc == SPTRSV_OK) rc = build_levels(P, d_rowptr, d_colidx, P->upper, P->fwd, s);
+    }
+    if (rc != SPTRSV_OK) {
+        destroy(P);
+        return rc;
+    }
+    P->analysis_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *plan = P;
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t sptrsv_free(sptrsv_plan_t plan) {
+    if (!plan) return SPTRSV_ERR_INVALID_ARG;
+    {
+        DeviceGuard g(plan->device);
+        cudaDeviceSynchronize();
+    }
+    destroy(plan);
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t sptrsv_solve(sptrsv_plan_t plan, const void* d_b, void* d_x, int nrhs, int ld,
+                             sptrsv_algo_t algo, void* stream) {
+    return solve_common(plan, false, d_b, d_x, nrhs, ld, algo, stream);
+}
+
+sptrsv_status_t sptrsv_solve_transpose(sptrsv_plan_t plan, const void* d_b, void* d_x, int nrhs,
+                                       int ld, sptrsv_algo_t algo, void* stream) {
+    return solve_common(plan, true, d_b, d_x, nrhs, ld, algo, stream);
+}
+
+sptrsv_status_t sptrsv_prepare_transpose(sptrsv_plan_t plan, void* stream) {
+    if (!plan) return SPTRSV_ERR_INVALID_ARG;
+    if (plan->n == 0) return SPTRSV_OK;
+    DeviceGuard g(plan->device);
+    return build_transpose(plan, (cudaStream_t)stream);
+}
+
+sptrsv_status_t sptrsv_grad_vals(sptrsv_plan_t plan, const void* d_y, const void* d_x, int nrhs,
+                                 int ld, void* d_gvals, void* stream) {
+    if (!plan || nrhs < 1 || ld < nrhs) return SPTRSV_ERR_INVALID_ARG;
+    if (plan->n == 0) return SPTRSV_OK;
+    if (!d_y || !d_x || (plan->nnz > 0 && !d_gvals)) return SPTRSV_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    CK(launch_grad_vals(plan->f64, plan->lanes, plan->n, plan->rowptr, plan->colidx, plan->unit,
+                        d_y, ld, d_x, ld, nrhs, d_gvals, (cudaStream_t)stream,
+                        plan->num_sms * 16));
+    plan->last_launches = 1;
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t sptrsv_residual(sptrsv_plan_t plan, const double* d_b, const double* d_x,
+                                double* d_r, int nrhs, int ld, void* stream) {
+    if (!plan || nrhs < 1 || ld < nrhs) return SPTRSV_ERR_INVALID_ARG;
+    if (!plan->f64) return SPTRSV_ERR_NOT_SUPPORTED;
+    if (plan->n == 0) return SPTRSV_OK;
+    if (!d_b || !d_x || !d_r) return SPTRSV_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    CK(launch_residual(plan->lanes, plan->n, plan->rowptr, plan->colidx,
+                       (const double*)plan->vals, plan->unit, nrhs, d_b, ld, d_x, ld, d_r, ld,
+                       nullptr, nullptr, false, plan->num_sms * 16, (cudaStream_t)stream));
+    plan->last_launches = 1;
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t sptrsv_refresh_values(sptrsv_plan_t plan, void* stream) {
+    if (!plan) return SPTRSV_ERR_INVALID_ARG;
+    if (!plan->vals32 || plan->nnz == 0) return SPTRSV_OK;
+    DeviceGuard g(plan->device);
+    CK(launch_to_f32(plan->nnz, 1, (const double*)plan->vals, 1, plan->vals32, nullptr,
+                     plan->num_sms * 16, (cudaStream_t)stream));
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t sptrsv_set_values(sptrsv_plan_t plan, const void* d_vals, void* stream) {
+    if (!plan || (plan->nnz > 0 && !d_vals)) return SPTRSV_ERR_INVALID_ARG;
+    plan->vals = d_vals;
+    return sptrsv_refresh_values(plan, stream);
+}
+
+sptrsv_status_t sptrsv_solve_refined(sptrsv_plan_t plan, const double* d_b, double* d_x,
+                                     int nrhs, int ld, int max_iter, double tol, int* iters,
+                                     double* rel_resid, void* stream) {
+    if (!plan || nrhs < 1 || ld < nrhs || max_iter < 0 || !(tol >= 0.0))
+        return SPTRSV_ERR_INVALID_ARG;
+    if (!plan->f64) return SPTRSV_ERR_NOT_SUPPORTED;
+    if (iters) *iters = 0;
+    if (rel_resid) *rel_resid = 0.0;
+    if (plan->n == 0) return SPTRSV_OK;
+    if (!d_b || !d_x || d_b == d_x) return SPTRSV_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (capturing(s)) return SPTRSV_ERR_NOT_SUPPORTED;
+    sptrsv_plan_t P = plan;
+    const int n = P->n;
+    const int grid = P->num_sms * 16;
+    if (!P->vals32 && P->nnz > 0) {
+        CK(cudaMalloc(&P->vals32, sizeof(float) * (size_t)P->nnz));
+        CK(launch_to_f32(P->nnz, 1, (const double*)P->vals, 1, P->vals32, nullptr, grid, s));
+    }
+    const size_t need = (size_t)n * nrhs;
+    if (P->rd_elems < need) {
+        CK(cudaStreamSynchronize(s));
+        cudaFree(P->r32);
+        cudaFree(P->d32);
+        P->r32 = P->d32 = nullptr;
+        P->rd_elems = 0;
+        CK(cudaMalloc(&P->r32, sizeof(float) * need));
+        CK(cudaMalloc(&P->d32, sizeof(float) * need));
+        P->rd_elems = need;
+    }
+    if (!P->stats) CK(cudaMalloc(&P->stats, 4 * sizeof(unsigned long long)));
+    CK(cudaMemsetAsync(P->stats, 0, 4 * sizeof(unsigned long long), s));
+    int launches = 0;
+    // x0 = 0, so r0 = b: the first FP32 solve is of b itself.
+    CK(launch_to_f32(n, nrhs, d_b, ld, P->r32, P->stats + 3, grid, s));
+    ST(run_solve(P, false, false, P->vals32, P->r32, nrhs, P->d32, nrhs, nrhs, SPTRSV_ALGO_SELF, s));
+    launches += 1 + P->last_launches;
+    CK(launch_update(n, nrhs, d_x, ld, P->d32, true, P->stats + 2, grid, s));
+    launches += 1;
+    int it = 0;
+    double rel = 0.0;
+    for (;;) {
+        CK(cudaMemsetAsync(P->stats, 0, sizeof(unsigned long long), s));
+        CK(launch_residual(P->lanes, n, P->rowptr, P->colidx, (const double*)P->vals, P->unit,
+                           nrhs, d_b, ld, d_x, ld, nullptr, 0, P->r32, P->stats, it == 0, grid,
+                           s));
+        launches += 1;
+        unsigned long long h[4];
+        CK(cudaMemcpyAsync(h, P->stats, sizeof(h), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        double st[4];
+        memcpy(st, h, sizeof(st));
+        const double denom = st[3] + st[1] * st[2];
+        rel = denom > 0.0 ? st[0] / denom : (st[0] > 0.0 ? INFINITY : 0.0);
+        if (rel <= tol || it >= max_iter) break;
+        ST(run_solve(P, false, false, P->vals32, P->r32, nrhs, P->d32, nrhs, nrhs,
+                     SPTRSV_ALGO_SELF, s));
+        launches += P->last_launches;
+        CK(cudaMemsetAsync(P->stats + 2, 0, sizeof(unsigned long long), s));
+        CK(launch_update(n, nrhs, d_x, ld, P->d32, false, P->stats + 2, grid, s));
+        launches += 1;
+        ++it;
+    }
+    if (iters) *iters = it;
+    if (rel_resid) *rel_resid = rel;
+    P->last_launches = launches;
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t sptrsv_set_tuning(sptrsv_plan_t plan, int lanes_per_row, int block_size,
+                                  int max_blocks) {
+    if (!plan) return SPTRSV_ERR_INVALID_ARG;
+    const int w = lanes_per_row;
+    if (!(w == 1 || w == 2 || w == 4 || w == 8 || w == 16 || w == 32)) return SPTRSV_ERR_INVALID_ARG;
+    if (block_size < 32 || block_size > 1024 || block_size % 32 != 0 || max_blocks < 0)
+        return SPTRSV_ERR_INVALID_ARG;
+    plan->lanes = w;
+    plan->block = block_size;
+    plan->max_blocks = max_blocks;
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t sptrsv_get_tuning(sptrsv_plan_t plan, int* lanes_per_row, int* block_size,
+                                  int* max_blocks) {
+    if (!plan) return SPTRSV_ERR_INVALID_ARG;
+    if (lanes_per_row) *lanes_per_row = plan->lanes;
+    if (block_size) *block_size = plan->block;
+    if (max_blocks) *max_blocks = plan->max_blocks;
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t sptrsv_set_spin_limit(sptrsv_plan_t plan, long long polls) {
+    if (!plan || polls < 1) return SPTRSV_ERR_INVALID_ARG;
+    plan->spin.limit = polls;
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t sptrsv_levels(sptrsv_plan_t plan, int transpose, int* nlev, const int** d_lev,
+                              const int** d_ilev, const int** d_jlev) {
+    if (!plan) return SPTRSV_ERR_INVALID_ARG;
+    if (transpose && !plan->has_trans && plan->n > 0) return SPTRSV_ERR_NOT_SUPPORTED;
+    const Levels& L = transpose ? plan->trn : plan->fwd;
+    if (nlev) *nlev = L.nlev;
+    if (d_lev) *d_lev = L.lev;
+    if (d_ilev) *d_ilev = L.ilev;
+    if (d_jlev) *d_jlev = L.jlev;
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t sptrsv_transpose_pattern(sptrsv_plan_t plan, const int** d_tptr,
+                                         const int** d_tidx, const int** d_tmap) {
+    if (!plan) return SPTRSV_ERR_INVALID_ARG;
+    if (!plan->has_trans && plan->n > 0) return SPTRSV_ERR_NOT_SUPPORTED;
+    if (d_tptr) *d_tptr = plan->tptr;
+    if (d_tidx) *d_tidx = plan->tidx;
+    if (d_tmap) *d_tmap = plan->tmap;
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t sptrsv_status(sptrsv_plan_t plan, void* stream, int* error_row) {
+    if (!plan) return SPTRSV_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    return take_status(plan, (cudaStream_t)stream, error_row);
+}
+
+int sptrsv_last_error_row(void) { return g_last_error_row; }
+
+const char* sptrsv_status_string(sptrsv_status_t status) {
+    switch (status) {
+        case SPTRSV_OK: return "SPTRSV_OK";
+        case SPTRSV_ERR_INVALID_ARG: return "SPTRSV_ERR_INVALID_ARG";
+        case SPTRSV_ERR_STRUCTURE: return "SPTRSV_ERR_STRUCTURE";
+        case SPTRSV_ERR_ZERO_PIVOT: return "SPTRSV_ERR_ZERO_PIVOT";
+        case SPTRSV_ERR_CUDA: return "SPTRSV_ERR_CUDA";
+        case SPTRSV_ERR_OOM: return "SPTRSV_ERR_OOM";
+        case SPTRSV_ERR_TIMEOUT: return "SPTRSV_ERR_TIMEOUT";
+        case SPTRSV_ERR_NOT_SUPPORTED: return "SPTRSV_ERR_NOT_SUPPORTED";
+        case SPTRSV_ERR_INTERNAL: return "SPTRSV_ERR_INTERNAL";
+    }
+    return "SPTRSV_ERR_UNKNOWN";
+}
+
+const char* sptrsv_last_cuda_error(void) { return g_last_cuda; }
+
+sptrsv_status_t sptrsv_analysis_ms(sptrsv_plan_t plan, double* ms) {
+    if (!plan || !ms) return SPTRSV_ERR_INVALID_ARG;
+    *ms = plan->analysis_ms;
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t sptrsv_profile_enable(sptrsv_plan_t plan, int enable) {
+    if (!plan) return SPTRSV_ERR_INVALID_ARG;
+    plan->prof = enable != 0;
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t sptrsv_profile_read(sptrsv_plan_t plan, double* total_ms, int* count) {
+    if (!plan) return SPTRSV_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    double tot = 0.0;
+    for (size_t k = 0; k < plan->ev_used; ++k) {
+        CK(cudaEventSynchronize(plan->ev[2 * k + 1]));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, plan->ev[2 * k], plan->ev[2 * k + 1]));
+        tot += ms;
+    }
+    if (total_ms) *total_ms = tot;
+    if (count) *count = (int)plan->ev_used;
+    plan->ev_used = 0;
+    return SPTRSV_OK;
+}
+
+int sptrsv_last_launch_count(sptrsv_plan_t plan) { return plan ? plan->last_launches : 0; }
+
+sptrsv_status_t sptrsv_debug_withhold_row(sptrsv_plan_t plan, int row) {
+    if (!plan || row < -1 || row >= plan->n) return SPTRSV_ERR_INVALID_ARG;
+    plan->withhold = row;
+    return SPTRSV_OK;
+}
+
+}  // extern "C"

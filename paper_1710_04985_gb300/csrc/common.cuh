@@ -1,0 +1,151 @@
+// Device helpers shared by the solver kernels: GPU-scope relaxed loads and
+// stores, the "not yet solved" marker, bounded dependency waits and the
+// status word.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sptrsv {
+
+// Status word: (row << 32) | code.  atomicMin keeps the lowest failing row
+// (and, for one row, the lowest code).  ~0ull means "no failure".
+constexpr unsigned long long kStatusClear = ~0ull;
+enum : int { kCodeStructure = 2, kCodeZeroPivot = 3, kCodeTimeout = 6, kCodeInternal = 8 };
+
+__device__ __forceinline__ void report(unsigned long long* status, int row, int code) {
+    unsigned long long v = ((unsigned long long)(unsigned)row << 32) | (unsigned)code;
+    atomicMin(status, v);
+}
+
+// ---------------------------------------------------------------------------
+// Relaxed loads/stores at GPU scope.  A relaxed access is single-copy atomic
+// for naturally aligned 4/8-byte words and is served by L2 (the coherence
+// point), never by a stale L1 line.  A published value is the only datum a
+// waiting row needs, so no acquire/release ordering is required.
+__device__ __forceinline__ double ld_relaxed(const double* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return __longlong_as_double((long long)v);
+}
+__device__ __forceinline__ float ld_relaxed(const float* p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return __uint_as_float(v);
+}
+__device__ __forceinline__ int ld_relaxed(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed(double* p, double v) {
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"((unsigned long long)__double_as_longlong(v)) : "memory");
+}
+__device__ __forceinline__ void st_relaxed(float* p, float v) {
+    asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(__float_as_uint(v)) : "memory");
+}
+__device__ __forceinline__ void st_relaxed(int* p, int v) {
+    asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// "Not yet solved" marker.  The self-scheduled solve fills x with all-ones
+// bit patterns (a NaN no arithmetic produces: NaN results are rewritten to
+// the canonical quiet NaN before they are published), so a published value
+// doubles as its own ready flag.
+template <typename T> struct Marker;
+template <> struct Marker<double> {
+    static __device__ __forceinline__ bool pending(double v) {
+        return (unsigned long long)__double_as_longlong(v) == ~0ull;
+    }
+    static __device__ __forceinline__ double pending_value() { return __longlong_as_double(-1ll); }
+    static __device__ __forceinline__ double canonical_nan() {
+        return __longlong_as_double(0x7ff8000000000000ll);
+    }
+};
+template <> struct Marker<float> {
+    static __device__ __forceinline__ bool pending(float v) { return __float_as_uint(v) == ~0u; }
+    static __device__ __forceinline__ float pending_value() { return __uint_as_float(~0u); }
+    static __device__ __forceinline__ float canonical_nan() { return __uint_as_float(0x7fc00000u); }
+};
+
+template <typename T>
+__device__ __forceinline__ T publishable(T v) {
+    return (v != v) ? Marker<T>::canonical_nan() : v;
+}
+
+// Spin policy of a dependency wait: a few hot polls, then polls spaced by a
+// growing __nanosleep (capped), at most `limit` polls in total.
+struct SpinPolicy {
+    long long limit;
+    int hot;          // polls before the first sleep
+    unsigned max_ns;  // back-off cap
+};
+
+// Waits until *p is published; on running out of polls records a timeout
+// for `row` and returns NaN (which then propagates to every later row, so
+// the whole solve still finishes).
+template <typename T>
+__device__ __forceinline__ T wait_value(const T* p, const SpinPolicy& sp,
+                                        unsigned long long* status, int row) {
+    T v = ld_relaxed(p);
+    if (!Marker<T>::pending(v)) return v;
+    long long it = 1;
+    unsigned ns = 32;
+    while (true) {
+        if (it >= sp.hot) {
+            __nanosleep(ns);
+            ns = ns < sp.max_ns ? ns * 2 : sp.max_ns;
+        }
+        v = ld_relaxed(p);
+        if (!Marker<T>::pending(v)) return v;
+        if (++it >= sp.limit) {
+            report(status, row, kCodeTimeout);
+            return Marker<T>::canonical_nan();
+        }
+    }
+}
+
+// Level analysis uses -1 as its "not yet computed" marker.
+__device__ __forceinline__ int wait_level(const int* p, const SpinPolicy& sp,
+                                          unsigned long long* status, int row) {
+    int v = ld_relaxed(p);
+    if (v >= 0) return v;
+    long long it = 1;
+    unsigned ns = 32;
+    while (true) {
+        if (it >= sp.hot) {
+            __nanosleep(ns);
+            ns = ns < sp.max_ns ? ns * 2 : sp.max_ns;
+        }
+        v = ld_relaxed(p);
+        if (v >= 0) return v;
+        if (++it >= sp.limit) {
+            report(status, row, kCodeTimeout);
+            return 0;
+        }
+    }
+}
+
+// Mask of the W-lane group (sub-warp) that `lane` belongs to.
+template <int W>
+__device__ __forceinline__ unsigned group_mask(int lane) {
+    if (W >= 32) return 0xffffffffu;
+    return ((1u << (W & 31)) - 1u) << ((lane / W) * W);
+}
+
+template <int W, typename T>
+__device__ __forceinline__ T group_sum(T v, unsigned mask) {
+#pragma unroll
+    for (int off = W / 2; off > 0; off >>= 1) v += __shfl_xor_sync(mask, v, off);
+    return v;
+}
+
+template <int W>
+__device__ __forceinline__ int group_max(int v, unsigned mask) {
+#pragma unroll
+    for (int off = W / 2; off > 0; off >>= 1) v = max(v, __shfl_xor_sync(mask, v, off));
+    return v;
+}
+
+}  // namespace sptrsv

@@ -1,0 +1,99 @@
+// Internal interface between the C-ABI host code (api.cu) and the kernel
+// translation units.  Not installed; not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace sptrsv {
+
+// Everything a solve kernel needs.  The pattern is either the user's CSR or
+// the plan's CSR of the transpose (then vmap maps entries to d_vals).
+struct SolveParams {
+    int n;
+    const int* ptr;
+    const int* idx;
+    const int* vmap;      // nullptr: entry q has value vals[q]
+    const void* vals;
+    int diag_first;       // upper-triangular pattern: diagonal is a row's first entry
+    int unit;
+    const int* jlev;      // rows in level order
+    const void* b;
+    long long ldb;
+    void* x;
+    long long ldx;
+    int nrhs;
+    int* ticket;          // self-scheduled: next row group to hand out
+    unsigned long long* status;
+    SpinPolicy spin;
+    int withhold;         // test hook: row whose result is never published (-1: none)
+    int kbeg, cnt;        // level-scheduled: this launch's slice of jlev
+};
+
+// ---- solve kernels (solve_self.cu, solve_level.cu, solve_mrhs.cu)
+cudaError_t launch_prep_self(bool f64, int n, int nrhs, void* x, long long ldx, const void* b,
+                             long long ldb, void* bcopy, int* ticket, int grid,
+                             cudaStream_t s);
+cudaError_t launch_self_k1(bool f64, int lanes, const SolveParams& p, int grid, int block,
+                           cudaStream_t s);
+cudaError_t launch_level_k1(bool f64, int lanes, const SolveParams& p, int block, cudaStream_t s);
+cudaError_t launch_mrhs(bool f64, int lanes, bool self, const SolveParams& p, int grid, int block,
+                        cudaStream_t s);
+// Resident blocks per SM of the kernel a launch with these choices would use.
+int self_blocks_per_sm(bool f64, int lanes, bool mrhs, bool map, int block);
+
+// ---- analysis kernels (analysis.cu)
+cudaError_t launch_validate(int n, int nnz, const int* ptr, const int* idx, const void* vals,
+                            bool f64, bool upper, bool unit, unsigned long long* status,
+                            int grid, cudaStream_t s);
+cudaError_t launch_level_sweep(int lanes, int n, const int* ptr, const int* idx, bool upper,
+                               int* lev, int* ticket, int* nlev, unsigned long long* status,
+                               SpinPolicy sp, int grid, int block, cudaStream_t s);
+int level_sweep_blocks_per_sm(int lanes, int block);
+// count[keys[e]] += 1 for keys in [0, bins); any other key is reported as
+// an internal error in *status and skipped.
+cudaError_t launch_histogram(const int* keys, int m, int* count, int bins,
+                             unsigned long long* status, cudaStream_t s);
+// out[0..m]: exclusive prefix sums of in[0..m-1], out[m] = total.
+cudaError_t launch_exclusive_scan(const int* in, int* out, int m, cudaStream_t s);
+// Stable LSD radix sort of (keys, values = vals_in or the identity) by the
+// low `bits` bits of the keys; sorted values land in vals_out.  Scratch:
+// 4 int arrays of m entries and one of radix_hist_entries(m) entries (x2).
+int radix_hist_entries(int m);
+cudaError_t radix_sort_values(const int* keys_in, const int* vals_in, int m, int bits,
+                              int* vals_out, int* k_a, int* v_a, int* k_b, int* v_b,
+                              int* hist, int* hist_scan, unsigned long long* status,
+                              cudaStream_t s);
+cudaError_t launch_iota(int* out, int m, cudaStream_t s);
+cudaError_t launch_row_of_entries(int n, const int* ptr, int* rowof, cudaStream_t s);
+// out[e] = src[index[e]] for index in [0, src_len); others reported.
+cudaError_t launch_gather(const int* src, int src_len, const int* index, int m, int* out,
+                          unsigned long long* status, cudaStream_t s);
+// Self-check of level sets: every position of jlev holds a row of the
+// level whose segment contains it, rows strictly increase inside a segment,
+// ilev[0] = 0 and ilev[nlev] = n.  Failures are reported as internal.
+cudaError_t launch_verify_levels(int n, int nlev, const int* lev, const int* ilev,
+                                 const int* jlev, unsigned long long* status, cudaStream_t s);
+
+// ---- auxiliary kernels (aux.cu)
+cudaError_t launch_grad_vals(bool f64, int lanes, int n, const int* ptr, const int* idx, bool unit,
+                             const void* y, long long ldy, const void* x, long long ldx, int k,
+                             void* g, cudaStream_t s, int grid);
+// r = b - A x in FP64; writes r (nullable, [n][ldr]) and r32 (nullable,
+// contiguous [n][k]); stats (nullable): atomicMax of max|r| into stats[0]
+// and, if want_norm, of max_i sum_j |A_ij| into stats[1].
+cudaError_t launch_residual(int lanes, int n, const int* ptr, const int* idx, const double* vals,
+                            bool unit, int k, const double* b, long long ldb, const double* x,
+                            long long ldx, double* r, long long ldr, float* r32,
+                            unsigned long long* stats, bool want_norm, int grid, cudaStream_t s);
+// x = d (first) or x += d, FP64 x [n][ldx], FP32 d contiguous [n][k];
+// atomicMax of max|x| into *xmax.
+cudaError_t launch_update(int n, int k, double* x, long long ldx, const float* d, bool first,
+                          unsigned long long* xmax, int grid, cudaStream_t s);
+// out32 = (float) in64 over [n][k] (in strided by ldin, out contiguous);
+// atomicMax of max|in| into *amax (nullable).
+cudaError_t launch_to_f32(int n, int k, const double* in, long long ldin, float* out,
+                          unsigned long long* amax, int grid, cudaStream_t s);
+
+}  // namespace sptrsv

@@ -1,0 +1,149 @@
+// Self-scheduled solve (Alg. 3, SLFR) for one right-hand side.
+//
+// Differences from the paper's SLFR kernel (Sec. 4.3), for sm_103a:
+//  * Rows are handed out in level order (jlev), as in the paper, but by a
+//    ticket counter rather than by warp index: a warp takes ticket t only
+//    while running, and every row it waits on belongs to a smaller ticket,
+//    already held by a running warp.  No residency assumption is needed.
+//  * No dependency counters and no CSC fan-out: the output x is pre-filled
+//    with a marker, and each lane waits directly on the x(j) it needs with a
+//    GPU-scope relaxed load.  The published value is its own ready flag, so
+//    a dependency costs one L2 round trip and no fence.
+//  * A row is reduced by a sub-warp of W lanes (W chosen per matrix), not by
+//    a whole warp, with shuffle reductions instead of shared memory; every
+//    wait is bounded.
+#include "internal.h"
+
+namespace sptrsv {
+
+template <typename T>
+__global__ void prep_self_k(int n, int nrhs, T* x, long long ldx, const T* b, long long ldb,
+                            T* bcopy, int* ticket) {
+    const long long total = (long long)n * nrhs;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    if (nrhs == 1) {
+        for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
+            if (bcopy) bcopy[e] = b[e * ldb];
+            x[e * ldx] = Marker<T>::pending_value();
+        }
+    } else {
+        for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
+            const long long r = e / nrhs;
+            const long long c = e - r * nrhs;
+            if (bcopy) bcopy[e] = b[r * ldb + c];
+            x[r * ldx + c] = Marker<T>::pending_value();
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *ticket = 0;
+}
+
+cudaError_t launch_prep_self(bool f64, int n, int nrhs, void* x, long long ldx, const void* b,
+                             long long ldb, void* bcopy, int* ticket, int grid, cudaStream_t s) {
+    long long want = ((long long)n * nrhs + 255) / 256;
+    int g = (int)(want < grid ? want : grid);
+    if (g < 1) g = 1;
+    if (f64)
+        prep_self_k<double><<<g, 256, 0, s>>>(n, nrhs, (double*)x, ldx, (const double*)b, ldb,
+                                              (double*)bcopy, ticket);
+    else
+        prep_self_k<float><<<g, 256, 0, s>>>(n, nrhs, (float*)x, ldx, (const float*)b, ldb,
+                                             (float*)bcopy, ticket);
+    return cudaGetLastError();
+}
+
+template <typename T, int W, bool MAP>
+__global__ void __launch_bounds__(1024) self_solve_k1(SolveParams p) {
+    constexpr int R = 32 / W;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane / W;
+    const int sl = lane - sub * W;
+    const unsigned gmask = group_mask<W>(lane);
+    const T* __restrict__ vals = (const T*)p.vals;
+    const T* b = (const T*)p.b;
+    T* x = (T*)p.x;
+    int t = 0;
+    if (lane == 0) t = atomicAdd(p.ticket, 1);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    while ((long long)t * R < p.n) {
+        int tn = 0;
+        if (lane == 0) tn = atomicAdd(p.ticket, 1);  // next ticket, consumed after this one
+        const long long k = (long long)t * R + sub;
+        if (k < p.n) {
+            const int i = p.jlev[k];
+            const int beg = p.ptr[i], end = p.ptr[i + 1];
+            T bi = T(0), di = T(1);
+            if (sl == 0) {
+                bi = b[(long long)i * p.ldb];
+                if (!p.unit) {
+                    const int q = p.diag_first ? beg : end - 1;
+                    di = vals[MAP ? p.vmap[q] : q];
+                }
+            }
+            T sum = T(0);
+            for (int q = beg + sl; q < end; q += W) {
+                const int c = p.idx[q];
+                if (c != i) {
+                    const T a = vals[MAP ? p.vmap[q] : q];
+                    const T xv = wait_value(x + (long long)c * p.ldx, p.spin, p.status, i);
+                    sum += a * xv;
+                }
+            }
+            sum = group_sum<W>(sum, gmask);
+            if (sl == 0) {
+                T xi = bi - sum;
+                if (!p.unit) xi = xi / di;
+                if (i != p.withhold) st_relaxed(x + (long long)i * p.ldx, publishable(xi));
+            }
+        }
+        t = __shfl_sync(0xffffffffu, tn, 0);
+    }
+}
+
+template <typename T, int W>
+static cudaError_t self_w(const SolveParams& p, int grid, int block, cudaStream_t s) {
+    if (p.vmap)
+        self_solve_k1<T, W, true><<<grid, block, 0, s>>>(p);
+    else
+        self_solve_k1<T, W, false><<<grid, block, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t self_t(int lanes, const SolveParams& p, int grid, int block, cudaStream_t s) {
+    switch (lanes) {
+        case 1: return self_w<T, 1>(p, grid, block, s);
+        case 2: return self_w<T, 2>(p, grid, block, s);
+        case 4: return self_w<T, 4>(p, grid, block, s);
+        case 8: return self_w<T, 8>(p, grid, block, s);
+        case 16: return self_w<T, 16>(p, grid, block, s);
+        case 32: return self_w<T, 32>(p, grid, block, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_self_k1(bool f64, int lanes, const SolveParams& p, int grid, int block,
+                           cudaStream_t s) {
+    return f64 ? self_t<double>(lanes, p, grid, block, s) : self_t<float>(lanes, p, grid, block, s);
+}
+
+template <typename T, bool MAP>
+static int occ_k1(int lanes, int block) {
+    int nb = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (lanes) {
+        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, self_solve_k1<T, 1, MAP>, block, 0); break;
+        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, self_solve_k1<T, 2, MAP>, block, 0); break;
+        case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, self_solve_k1<T, 4, MAP>, block, 0); break;
+        case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, self_solve_k1<T, 8, MAP>, block, 0); break;
+        case 16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, self_solve_k1<T, 16, MAP>, block, 0); break;
+        case 32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, self_solve_k1<T, 32, MAP>, block, 0); break;
+    }
+    return (e == cudaSuccess && nb > 0) ? nb : 1;
+}
+
+int self_k1_blocks_per_sm(bool f64, int lanes, bool map, int block) {
+    if (f64) return map ? occ_k1<double, true>(lanes, block) : occ_k1<double, false>(lanes, block);
+    return map ? occ_k1<float, true>(lanes, block) : occ_k1<float, false>(lanes, block);
+}
+
+}  // namespace sptrsv

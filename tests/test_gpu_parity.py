@@ -1,0 +1,395 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Levels and level sets must match bit for bit; FP64 solves within
+max|x - x_ref| / max|x_ref| <= 1e-12; FP32 solves within 1e-4 of the FP64
+oracle.  Sizes span many tiles and ragged tails; edge cases cover empty,
+single-row, diagonal (nlev = 1), bidiagonal (nlev = n), maximum-length rows
+and unit diagonals that are not stored.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_util import (TOL32, TOL64, assert_levels_equal, bidiagonal, dev, diagonal, long_rows,
+                      plan_for, relerr, tensors, unit_without_diagonal)
+
+pytestmark = pytest.mark.gpu
+
+
+def _ilu_small():
+    return synth.lap3d_7pt_ilu0(16, 12, 10)
+
+
+MATRICES = {
+    "workload0": lambda: synth.workload0()[0],
+    "ilu_L": lambda: _ilu_small()[0],
+    "ilu_U": lambda: _ilu_small()[1],
+    "general": lambda: synth.general_lower(20011, 7),
+    "general_upper": lambda: synth.to_upper_by_reversal(synth.general_lower(9001, 8)),
+    "bidiag": lambda: bidiagonal(3001),
+    "bidiag_upper": lambda: bidiagonal(1777, upper=True),
+    "diag": lambda: diagonal(5000),
+    "long_rows": long_rows,
+    "unit_nodiag": unit_without_diagonal,
+    "lap2d_upper": lambda: synth.lap2d_5pt_upper(37, 29),
+}
+
+_cache = {}
+
+
+def mat(name):
+    if name not in _cache:
+        _cache[name] = MATRICES[name]()
+    return _cache[name]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu(cuda_device):
+    yield
+
+
+# ---------------------------------------------------------------- levels
+
+@pytest.mark.parametrize("name", list(MATRICES))
+def test_levels_bit_exact(name):
+    A = mat(name)
+    with plan_for(A) as p:
+        assert_levels_equal(p.levels(), A)
+
+
+@pytest.mark.parametrize("name", ["workload0", "ilu_L", "ilu_U", "general", "general_upper",
+                                  "bidiag", "long_rows", "unit_nodiag"])
+def test_transpose_levels_and_pattern(name):
+    A = mat(name)
+    with plan_for(A) as p:
+        p.prepare_transpose()
+        assert_levels_equal(p.levels(transpose=True), A, transpose=True)
+        tptr, tidx, tmap = (t.cpu().numpy() for t in p.transpose_pattern())
+        T = A.scipy().T.tocsr()
+        T.sort_indices()
+        assert np.array_equal(tptr, T.indptr)
+        assert np.array_equal(tidx, T.indices)
+        assert np.array_equal(A.vals[tmap], T.data)
+
+
+# ---------------------------------------------------------------- solves
+
+@pytest.mark.parametrize("algo", ["self", "level"])
+@pytest.mark.parametrize("name", list(MATRICES))
+def test_solve_fp64(name, algo):
+    A = mat(name)
+    b = synth.uniform(A.n, 11)
+    ref = oracle.solve(A.rowptr, A.colidx, A.vals, b, upper=A.upper, unit=A.unit)
+    with plan_for(A) as p:
+        x = p.solve(torch.tensor(b, device=dev()), algo=algo)
+        assert relerr(x, ref) <= TOL64
+        assert p.status() == (0, -1)
+
+
+@pytest.mark.parametrize("algo", ["self", "level"])
+@pytest.mark.parametrize("name", ["general", "ilu_L", "ilu_U", "long_rows"])
+def test_solve_fp32(name, algo):
+    A = mat(name)
+    b = synth.uniform(A.n, 12)
+    ref = oracle.solve(A.rowptr, A.colidx, A.vals, b, upper=A.upper, unit=A.unit)
+    with plan_for(A, torch.float32) as p:
+        x = p.solve(torch.tensor(b, device=dev(), dtype=torch.float32), algo=algo)
+        assert relerr(x.double(), ref) <= TOL32
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("block", [64, 256, 1024])
+def test_every_launch_shape(lanes, block):
+    A = mat("general")
+    b = synth.uniform(A.n, 13)
+    ref = oracle.solve(A.rowptr, A.colidx, A.vals, b)
+    with plan_for(A) as p:
+        p.set_tuning(lanes, block, 0)
+        bt = torch.tensor(b, device=dev())
+        for algo in ("self", "level"):
+            assert relerr(p.solve(bt, algo=algo), ref) <= TOL64
+        p.set_tuning(lanes, block, 3)          # a tiny persistent grid still finishes
+        assert relerr(p.solve(bt), ref) <= TOL64
+
+
+@pytest.mark.parametrize("k", [2, 3, 8, 32, 33])
+@pytest.mark.parametrize("algo", ["self", "level"])
+def test_multi_rhs(k, algo):
+    for name in ("general", "ilu_U"):
+        A = mat(name)
+        b = synth.uniform((A.n, k), 14 + k)
+        ref = oracle.solve(A.rowptr, A.colidx, A.vals, b, upper=A.upper, unit=A.unit)
+        with plan_for(A) as p:
+            x = p.solve(torch.tensor(b, device=dev()), algo=algo)
+            assert relerr(x, ref) <= TOL64
+
+
+@pytest.mark.parametrize("algo", ["self", "level"])
+def test_leading_dimension_and_in_place(algo):
+    A = mat("general")
+    k, ld = 3, 5
+    b = synth.uniform((A.n, k), 15)
+    ref = oracle.solve(A.rowptr, A.colidx, A.vals, b)
+    with plan_for(A) as p:
+        big = torch.zeros((A.n, ld), dtype=torch.float64, device=dev())
+        big[:, :k] = torch.tensor(b, device=dev())
+        out = torch.full((A.n, ld), 7.0, dtype=torch.float64, device=dev())
+        p.solve(big[:, :k], out=out[:, :k], algo=algo)
+        assert relerr(out[:, :k], ref) <= TOL64
+        assert torch.all(out[:, k:] == 7.0)          # untouched padding columns
+        inplace = big[:, :k]
+        p.solve(inplace, out=inplace, algo=algo)      # x == b
+        assert relerr(inplace, ref) <= TOL64
+        v = torch.tensor(b[:, 0].copy(), device=dev())
+        p.solve(v, out=v, algo=algo)
+        assert relerr(v, ref[:, 0]) <= TOL64
+
+
+@pytest.mark.parametrize("algo", ["self", "level"])
+@pytest.mark.parametrize("name", ["workload0", "ilu_L", "ilu_U", "general", "general_upper",
+                                  "long_rows", "unit_nodiag", "bidiag"])
+def test_solve_transpose(name, algo):
+    A = mat(name)
+    for k in (1, 4):
+        g = synth.uniform((A.n, k) if k > 1 else A.n, 16)
+        ref = oracle.solve_transpose(A.rowptr, A.colidx, A.vals, g, upper=A.upper, unit=A.unit)
+        with plan_for(A) as p:
+            y = p.solve_transpose(torch.tensor(g, device=dev()), algo=algo)
+            assert relerr(y, ref) <= TOL64
+
+
+def test_bitwise_determinism_and_algo_agreement():
+    """The pull form fixes each row's reduction order: repeated solves, and
+    the level- and self-scheduled forms at the same width, agree bit for bit."""
+    A = mat("general")
+    with plan_for(A) as p:
+        bt = torch.tensor(synth.uniform(A.n, 17), device=dev())
+        first = p.solve(bt).clone()
+        for _ in range(20):
+            assert torch.equal(p.solve(bt), first)
+        assert torch.equal(p.solve(bt, algo="level"), first)
+
+
+# ---------------------------------------------------------------- edge cases
+
+def test_empty_matrix():
+    from paper_1710_04985_gb300 import TriangularPlan
+    d = dev()
+    p = TriangularPlan(torch.zeros(1, dtype=torch.int32, device=d),
+                       torch.zeros(0, dtype=torch.int32, device=d),
+                       torch.zeros(0, dtype=torch.float64, device=d))
+    assert p.levels()["nlev"] == 0
+    out = p.solve(torch.zeros(0, dtype=torch.float64, device=d))
+    assert out.numel() == 0
+    p.close()
+
+
+def test_single_row_and_values_update():
+    A = synth.CSR(1, np.array([0, 1], np.int32), np.array([0], np.int32), np.array([4.0]))
+    with plan_for(A) as p:
+        for algo in ("self", "level"):
+            x = p.solve(torch.tensor([2.0], device=dev(), dtype=torch.float64), algo=algo)
+            assert x.item() == 0.5
+        p.set_values(torch.tensor([8.0], device=dev(), dtype=torch.float64))
+        assert p.solve(torch.tensor([2.0], device=dev(), dtype=torch.float64)).item() == 0.25
+
+
+def test_values_change_without_reanalysis():
+    """Sec. 1: ILU refactorisation keeps the pattern; solves see new values."""
+    A = mat("general")
+    with plan_for(A) as p:
+        b = synth.uniform(A.n, 18)
+        bt = torch.tensor(b, device=dev())
+        p.solve(bt)
+        p.vals.mul_(2.0)
+        ref = oracle.solve(A.rowptr, A.colidx, 2.0 * A.vals, b)
+        assert relerr(p.solve(bt), ref) <= TOL64
+
+
+def _bad(n, rows, cols, vals, upper=False, unit=False):
+    rows = np.asarray(rows)
+    rowptr = np.zeros(n + 1, dtype=np.int32)
+    np.cumsum(np.bincount(rows, minlength=n), out=rowptr[1:])
+    return synth.CSR(n, rowptr, np.asarray(cols, np.int32), np.asarray(vals, float),
+                     upper=upper, unit=unit)
+
+
+@pytest.mark.parametrize("case,code,row", [
+    ("unsorted", 2, 2), ("duplicate", 2, 1), ("upper_entry_in_lower", 2, 1),
+    ("column_out_of_range", 2, 2), ("missing_diagonal", 3, 1), ("zero_diagonal", 3, 2),
+    ("lower_entry_in_upper", 2, 1),
+])
+def test_structural_errors(case, code, row):
+    from paper_1710_04985_gb300 import SptrsvError
+    cases = {
+        "unsorted": _bad(3, [0, 1, 1, 2, 2, 2], [0, 0, 1, 1, 0, 2], [1, 1, 1, 1, 1, 1]),
+        "duplicate": _bad(3, [0, 1, 1, 1, 2], [0, 0, 0, 1, 2], [1, 1, 1, 1, 1]),
+        "upper_entry_in_lower": _bad(3, [0, 1, 1, 2], [0, 1, 2, 2], [1, 1, 1, 1]),
+        "column_out_of_range": _bad(3, [0, 1, 2, 2], [0, 1, 2, 9], [1, 1, 1, 1]),
+        "missing_diagonal": _bad(3, [0, 1, 2], [0, 0, 2], [1, 1, 1]),
+        "zero_diagonal": _bad(3, [0, 1, 2, 2], [0, 1, 1, 2], [1, 1, 1, 0.0]),
+        "lower_entry_in_upper": _bad(3, [0, 1, 1, 2], [0, 0, 1, 2], [1, 1, 1, 1], upper=True),
+    }
+    with pytest.raises(SptrsvError) as ei:
+        plan_for(cases[case])
+    assert ei.value.status == code and ei.value.row == row
+
+
+def test_bad_rowptr():
+    from paper_1710_04985_gb300 import SptrsvError
+    A = synth.CSR(3, np.array([0, 2, 1, 3], np.int32), np.array([0, 0, 1], np.int32),
+                  np.ones(3))
+    with pytest.raises(SptrsvError) as ei:
+        plan_for(A)
+    assert ei.value.status == 2
+
+
+def test_timeout_is_reported_and_solve_finishes():
+    """A row that is never published: every row that depends on it gives up
+    after the spin limit, records SPTRSV_ERR_TIMEOUT and publishes NaN; rows
+    independent of it are still exact.  The GPU stays usable."""
+    A = bidiagonal(2000)
+    withheld = 300
+    with plan_for(A) as p:
+        p.set_spin_limit(1 << 14)
+        p.withhold_row(withheld)
+        b = synth.uniform(A.n, 19)
+        x = p.solve(torch.tensor(b, device=dev())).cpu().numpy()
+        st, row = p.status()
+        assert st == 6 and row == withheld + 1
+        ref = oracle.solve(A.rowptr, A.colidx, A.vals, b)
+        assert relerr(x[:withheld], ref[:withheld]) <= TOL64
+        assert np.all(np.isnan(x[withheld + 1:]))
+        p.withhold_row(-1)
+        assert relerr(p.solve(torch.tensor(b, device=dev())), ref) <= TOL64
+        assert p.status() == (0, -1)
+
+
+# ---------------------------------------------------------------- gradient / residual
+
+@pytest.mark.parametrize("name", ["general", "ilu_L", "ilu_U", "unit_nodiag"])
+def test_grad_vals_matches_oracle(name):
+    A = mat(name)
+    for k in (1, 3):
+        y = synth.uniform((A.n, k), 20)
+        x = synth.uniform((A.n, k), 21)
+        ref = oracle.grad_vals(A.rowptr, A.colidx, y, x, unit=A.unit)
+        with plan_for(A) as p:
+            g = p.grad_vals(torch.tensor(y, device=dev()), torch.tensor(x, device=dev()))
+            assert relerr(g, ref) <= 1e-14
+
+
+def test_residual_matches_oracle():
+    A = mat("general")
+    b = synth.uniform((A.n, 2), 22)
+    x = synth.uniform((A.n, 2), 23)
+    ref = oracle.residual(A.rowptr, A.colidx, A.vals, b, x)
+    with plan_for(A) as p:
+        r = p.residual(torch.tensor(b, device=dev()), torch.tensor(x, device=dev()))
+        assert relerr(r, ref) <= 1e-14
+
+
+@pytest.mark.parametrize("transpose", [False, True])
+def test_autograd_against_oracle_and_finite_differences(transpose):
+    from paper_1710_04985_gb300 import sparse_triangular_solve
+    A = mat("general")
+    b = synth.uniform(A.n, 24)
+    t = synth.uniform(A.n, 25)
+    with plan_for(A) as p:
+        v = torch.tensor(A.vals, device=dev()).requires_grad_(True)
+        bb = torch.tensor(b, device=dev()).requires_grad_(True)
+        tt = torch.tensor(t, device=dev())
+        x = sparse_triangular_solve(p, v, bb, transpose=transpose)
+        loss = 0.5 * ((x - tt) ** 2).sum()
+        loss.backward()
+        if transpose:
+            xr = oracle.solve_transpose(A.rowptr, A.colidx, A.vals, b)
+            yr = oracle.solve(A.rowptr, A.colidx, A.vals, xr - t)
+            gr = oracle.grad_vals(A.rowptr, A.colidx, xr, yr)
+        else:
+            xr = oracle.solve(A.rowptr, A.colidx, A.vals, b)
+            yr = oracle.solve_transpose(A.rowptr, A.colidx, A.vals, xr - t)
+            gr = oracle.grad_vals(A.rowptr, A.colidx, yr, xr)
+        assert relerr(bb.grad, yr) <= TOL64
+        assert relerr(v.grad, gr) <= TOL64
+        # central differences through the GPU solve
+        rng = np.random.default_rng(26)
+
+        def L(vals, bvec):
+            with torch.no_grad():
+                xx = sparse_triangular_solve(p, vals, bvec, transpose=transpose)
+                return 0.5 * float(((xx - tt) ** 2).sum())
+
+        v0 = v.detach().clone()
+        b0 = bb.detach().clone()
+        for q in rng.choice(A.nnz, 8, replace=False):
+            h = 1e-5 * max(1.0, abs(A.vals[q]))
+            vp, vm = v0.clone(), v0.clone()
+            vp[q] += h
+            vm[q] -= h
+            fd = (L(vp, b0) - L(vm, b0)) / (2 * h)
+            an = float(v.grad[q])
+            assert abs(fd - an) <= 1e-4 * max(1.0, abs(an))
+        for q in rng.choice(A.n, 8, replace=False):
+            h = 1e-5
+            bp, bm = b0.clone(), b0.clone()
+            bp[q] += h
+            bm[q] -= h
+            fd = (L(v0, bp) - L(v0, bm)) / (2 * h)
+            an = float(bb.grad[q])
+            assert abs(fd - an) <= 1e-4 * max(1.0, abs(an))
+
+
+# ---------------------------------------------------------------- precision
+
+@pytest.mark.parametrize("name", ["general", "ilu_L", "ilu_U", "long_rows"])
+@pytest.mark.parametrize("k", [1, 8])
+def test_fp32_with_fp64_refinement(name, k):
+    A = mat(name)
+    b = synth.uniform((A.n, k) if k > 1 else A.n, 27)
+    ref = oracle.solve(A.rowptr, A.colidx, A.vals, b, upper=A.upper, unit=A.unit)
+    with plan_for(A) as p:
+        x, iters, rel = p.solve_refined(torch.tensor(b, device=dev()))
+        err = relerr(x, ref)
+        assert err <= TOL64, (err, iters, rel)
+        assert 1 <= iters <= 10
+
+
+# ---------------------------------------------------------------- batching
+
+def test_batched_block_diagonal_graph():
+    from paper_1710_04985_gb300 import BatchedTriangularSolve
+    mats = synth.batch_general(24, seed=31, nmin=1000, nmax=8000)
+    systems = [(m.rowptr, m.colidx, m.vals) for m in mats]
+    bs = BatchedTriangularSolve(systems, tune=True)
+    assert bs.tuning["best"][0] in (1, 2, 4, 8, 16, 32)
+    bvecs = [synth.uniform(m.n, 100 + s) for s, m in enumerate(mats)]
+    x = bs.solve(torch.tensor(np.concatenate(bvecs), device=dev())).cpu().numpy()
+    lev = bs.plan.levels()["lev"].cpu().numpy()
+    off = bs.offsets
+    for s, m in enumerate(mats):
+        ref = oracle.solve(m.rowptr, m.colidx, m.vals, bvecs[s])
+        assert relerr(x[off[s]:off[s + 1]], ref) <= TOL64
+        lref, _ = oracle.levels(m.rowptr, m.colidx)
+        assert np.array_equal(lev[off[s]:off[s + 1]], lref)
+    # replay with new right-hand sides
+    b2 = [synth.uniform(m.n, 200 + s) for s, m in enumerate(mats)]
+    x2 = bs.solve(torch.tensor(np.concatenate(b2), device=dev())).cpu().numpy()
+    for s in (0, len(mats) - 1):
+        m = mats[s]
+        ref = oracle.solve(m.rowptr, m.colidx, m.vals, b2[s])
+        assert relerr(x2[off[s]:off[s + 1]], ref) <= TOL64
+
+
+def test_autotuner_keeps_results_exact():
+    from paper_1710_04985_gb300 import autotune
+    A = mat("ilu_L")
+    b = synth.uniform(A.n, 32)
+    ref = oracle.solve(A.rowptr, A.colidx, A.vals, b, unit=True)
+    with plan_for(A) as p:
+        bt = torch.tensor(b, device=dev())
+        res = autotune.tune(p, bt, use_cache=False, blocks=(128, 256))
+        assert len(res["table"]) == 12 and p.tuning["lanes_per_row"] == res["best"][0]
+        assert relerr(p.solve(bt), ref) <= TOL64
