@@ -312,7 +312,8 @@ def main():
                        "nlev": [pl.levels()["nlev"], pu.levels()["nlev"]],
                        "step": "y = U^-1 (L^-1 b), eq. (3): 2 triangular solves",
                        "algo": "self-scheduled (Alg. 3)",
-                       "tuning": {"L": list(tune_l[:2]), "U": list(tune_u[:2])},
+                       "tuning": {"L": list(tune_l[:3]), "U": list(tune_u[:3]),
+                                  "fields": ["lanes_per_row", "block", "max_blocks"]},
                        "l2": "inputs larger than L2 (2 x 150 MB of matrix+vectors per step)",
                        "parallelism": f"replicas x{world}"},
             "effective_gbs": value / world * bytes_solve / 1e9 * world,

@@ -194,18 +194,20 @@ SPTRSV_API sptrsv_status_t sptrsv_refresh_values(sptrsv_plan_t plan, void *strea
  * row is reduced by a sub-warp of that many lanes, so one warp holds
  * 32 / lanes_per_row rows; block_size a multiple of 32 in [32, 1024];
  * max_blocks caps the persistent grid of the self-scheduled solve (0 = as
- * many as fit on the device at once).  Applies to the forward and the
- * transposed solves.  Multi-RHS solves pick their own width from nrhs. */
+ * many as fit on the device at once; the default is 2 blocks per SM, which
+ * keeps enough rows waiting ahead of the dependency frontier without
+ * flooding L2 with polls).  Applies to the forward and the transposed
+ * solves.  Multi-RHS solves pick their own width from nrhs. */
 SPTRSV_API sptrsv_status_t sptrsv_set_tuning(sptrsv_plan_t plan, int lanes_per_row,
                                   int block_size, int max_blocks);
 SPTRSV_API sptrsv_status_t sptrsv_get_tuning(sptrsv_plan_t plan, int *lanes_per_row,
                                   int *block_size, int *max_blocks);
 
-/* Upper bound on the polls of one dependency wait before the wait gives up,
- * records SPTRSV_ERR_TIMEOUT with its row and publishes NaN so that every
- * later row still finishes.  Default 2^24 (several seconds with the
- * built-in back-off); the environment variable SPTRSV_SPIN_LIMIT overrides
- * the default for new plans. */
+/* Upper bound on the polling rounds of one dependency wait before the wait
+ * gives up, records SPTRSV_ERR_TIMEOUT with its row and goes on with NaN so
+ * that every later row still finishes.  Default 2^24 rounds (several
+ * seconds); the environment variable SPTRSV_SPIN_LIMIT overrides the
+ * default for new plans. */
 SPTRSV_API sptrsv_status_t sptrsv_set_spin_limit(sptrsv_plan_t plan, long long polls);
 
 /* -------------------------------------------------------------- inspection */

@@ -69,43 +69,139 @@ cudaError_t launch_validate(int n, int nnz, const int* ptr, const int* idx, cons
 // order) from a ticket counter.  Every dependency of a row comes earlier in
 // that order, and every earlier ticket is held by a running warp, so the
 // sweep cannot deadlock whatever the residency.  lev[] starts at -1
-// ("unknown"); a row publishes its level with one relaxed store.
+// ("unknown"); a row publishes its level with one relaxed store.  As in the
+// self-scheduled solve, the warp stays converged in one round loop.  Rows of
+// one ticket are consecutive, so they often depend on each other (a chain
+// along a grid line, a band): such a dependency is served by a warp shuffle
+// from the lane that owns the row as soon as it is published, instead of an
+// L2 round trip.
 template <int W>
 __global__ void level_sweep_k(int n, const int* __restrict__ ptr, const int* __restrict__ idx,
                               int upper, int* lev, int* ticket, int* nlev,
                               unsigned long long* status, SpinPolicy sp) {
     constexpr int R = 32 / W;
+    constexpr int E = kChunk;
+    constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const int sub = lane / W;
-    const int sl = lane - sub * W;
+    const int grp = lane / W;
+    const int sl = lane - grp * W;
     const unsigned gmask = group_mask<W>(lane);
     int local_max = -1;
     int t = 0;
     if (lane == 0) t = atomicAdd(ticket, 1);
-    t = __shfl_sync(0xffffffffu, t, 0);
+    t = __shfl_sync(FULL, t, 0);
     while ((long long)t * R < n) {
         int tn = 0;
         if (lane == 0) tn = atomicAdd(ticket, 1);
-        const long long q = (long long)t * R + sub;
-        if (q < n) {
-            const int i = upper ? n - 1 - (int)q : (int)q;
-            const int beg = ptr[i], end = ptr[i + 1];
-            int m = -1;
-            for (int e = beg + sl; e < end; e += W) {
-                const int c = idx[e];
-                if (c != i) m = max(m, wait_level(lev + c, sp, status, i));
+        // rows of this ticket: first = t*R in substitution order
+        const int first = (int)((long long)t * R);
+        const int rows = (n - first) < R ? (n - first) : R;
+        const bool has_row = grp < rows;
+        const int i0 = upper ? n - 1 - first : first;  // row of group 0
+        int i = 0, beg = 0, end = 0;
+        if (has_row) {
+            i = upper ? i0 - grp : i0 + grp;
+            beg = ptr[i];
+            end = ptr[i + 1];
+        }
+        int q0 = beg + sl;
+        int c[E], v[E];
+        unsigned live = 0, pend = 0, local = 0;  // local: dependency inside this ticket
+        auto load_chunk = [&]() {
+            live = pend = local = 0;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int qq = q0 + e * W;
+                c[e] = -1;
+                v[e] = -1;
+                if (qq < end) {
+                    const int cc = idx[qq];
+                    if (cc != i) {
+                        c[e] = cc;
+                        live |= 1u << e;
+                        const int g2 = upper ? i0 - cc : cc - i0;  // owning group, if in ticket
+                        if (g2 >= 0 && g2 < grp) local |= 1u << e;
+                    }
+                }
             }
-            m = group_max<W>(m, gmask);
-            if (sl == 0) {
-                st_relaxed(lev + i, m + 1);
-                local_max = max(local_max, m + 1);
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                if ((live & ~local) & (1u << e)) v[e] = ld_relaxed(lev + c[e]);
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                if ((live & (1u << e)) && v[e] < 0) pend |= 1u << e;
+        };
+        bool lane_done = q0 >= end;
+        if (!lane_done) load_chunk();
+        bool published = !has_row;
+        int pub = -1;  // this group's level once published (same on all its lanes)
+        int m = -1;
+        long long waits = 0;
+        unsigned ns = 32;
+        while (true) {
+            if (!lane_done && pend == 0) {
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    if (live & (1u << e)) m = max(m, v[e]);
+                q0 += W * E;
+                if (q0 >= end) lane_done = true;
+                else load_chunk();
+            }
+            const unsigned done = __ballot_sync(FULL, lane_done);
+            const bool row_ready = (done & gmask) == gmask;
+            const int tot = group_max<W>(m, FULL);
+            if (row_ready && !published) {
+                pub = tot + 1;
+                if (sl == 0) {
+                    st_relaxed(lev + i, pub);
+                    local_max = max(local_max, pub);
+                }
+                published = true;
+            }
+            if (__all_sync(FULL, published)) break;
+            // dependencies inside the ticket: read the owner's level by shuffle
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const bool want = (pend & local & (1u << e)) != 0;
+                const int g2 = want ? (upper ? i0 - c[e] : c[e] - i0) : grp;
+                const int got = __shfl_sync(FULL, pub, g2 * W);
+                if (want && got >= 0) {
+                    v[e] = got;
+                    pend &= ~(1u << e);
+                }
+            }
+            if (__any_sync(FULL, (pend & ~local) != 0)) {
+                const unsigned far = pend & ~local;
+                if (far) {
+#pragma unroll
+                    for (int e = 0; e < E; ++e)
+                        if (far & (1u << e)) v[e] = ld_relaxed(lev + c[e]);
+#pragma unroll
+                    for (int e = 0; e < E; ++e)
+                        if ((far & (1u << e)) && v[e] >= 0) pend &= ~(1u << e);
+                }
+                if (++waits >= sp.limit) {
+                    if (far) {
+                        report(status, i, kCodeTimeout);
+#pragma unroll
+                        for (int e = 0; e < E; ++e)
+                            if (far & (1u << e)) v[e] = 0;
+                        pend &= local;
+                    }
+                } else if (waits >= sp.hot) {
+                    __nanosleep(ns);
+                    ns = ns < sp.max_ns ? ns * 2 : sp.max_ns;
+                }
+            } else {
+                waits = 0;
+                ns = 32;
             }
         }
-        t = __shfl_sync(0xffffffffu, tn, 0);
+        t = __shfl_sync(FULL, tn, 0);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1)
-        local_max = max(local_max, __shfl_xor_sync(0xffffffffu, local_max, off));
+        local_max = max(local_max, __shfl_xor_sync(FULL, local_max, off));
     if (lane == 0 && local_max >= 0) atomicMax(nlev, local_max + 1);
 }
 

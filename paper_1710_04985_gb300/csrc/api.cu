@@ -119,7 +119,7 @@ struct sptrsv_plan_s {
     size_t rd_elems = 0;
     unsigned long long* stats = nullptr;  // [0] max|r| [1] |A|_inf [2] max|x| [3] max|b|
     int lanes = 4, block = 256, max_blocks = 0;
-    SpinPolicy spin{1ll << 24, 16, 256};
+    SpinPolicy spin{1ll << 24, 256, 128};
     int withhold = -1;
     double analysis_ms = 0.0;
     bool prof = false;
@@ -178,12 +178,20 @@ sptrsv_status_t build_levels(sptrsv_plan_t P, const int* ptr, const int* idx, bo
     CK(cudaMalloc(&L.lev, sizeof(int) * (size_t)n));
     CK(cudaMemsetAsync(L.lev, 0xff, sizeof(int) * (size_t)n, s));
     CK(cudaMemsetAsync(P->counters, 0, 2 * sizeof(int), s));
-    const int lanes = P->lanes;
+    // One lane per ~4 entries of an average row (a chunk), so short rows get a
+    // lane each and a ticket holds many consecutive rows; a moderate grid
+    // keeps the polling traffic down.
+    int lanes = (int)env_ll("SPTRSV_SWEEP_LANES", 0);
+    if (!(lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8 || lanes == 16 || lanes == 32))
+        lanes = pow2_at_least(((double)P->nnz / (n > 0 ? n : 1) - 1.0) / kChunk);
     const int block = 256;
     const int R = 32 / lanes;
     const long long tickets = ((long long)n + R - 1) / R;
     const long long want_blocks = (tickets + block / 32 - 1) / (block / 32);
-    long long grid = (long long)level_sweep_blocks_per_sm(lanes, block) * P->num_sms;
+    long long per_sm = env_ll("SPTRSV_SWEEP_BLOCKS_PER_SM", 4);
+    const long long fit = level_sweep_blocks_per_sm(lanes, block);
+    if (per_sm > fit) per_sm = fit;
+    long long grid = per_sm * P->num_sms;
     if (grid > want_blocks) grid = want_blocks;
     if (grid < 1) grid = 1;
     CK(launch_level_sweep(lanes, n, ptr, idx, upper, L.lev, P->counters, P->counters + 1,
@@ -424,9 +432,10 @@ sptrsv_status_t sptrsv_analyze(int n, int nnz, const int* d_rowptr, const int* d
     P->colidx = d_colidx;
     P->vals = d_vals;
     P->lanes = default_lanes(n, nnz);
+    P->max_blocks = 2 * P->num_sms;
     P->spin.limit = env_ll("SPTRSV_SPIN_LIMIT", 1ll << 24);
-    P->spin.hot = (int)env_ll("SPTRSV_SPIN_HOT", 16);
-    P->spin.max_ns = (unsigned)env_ll("SPTRSV_SPIN_MAX_NS", 256);
+    P->spin.hot = (int)env_ll("SPTRSV_SPIN_HOT", 256);
+    P->spin.max_ns = (unsigned)env_ll("SPTRSV_SPIN_MAX_NS", 128);
     sptrsv_status_t rc = SPTRSV_OK;
     e = cudaMalloc(&P->counters, 4 * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&P->status, sizeof(unsigned long long));

@@ -74,58 +74,18 @@ __device__ __forceinline__ T publishable(T v) {
     return (v != v) ? Marker<T>::canonical_nan() : v;
 }
 
-// Spin policy of a dependency wait: a few hot polls, then polls spaced by a
-// growing __nanosleep (capped), at most `limit` polls in total.
+// Spin policy of a dependency wait: a few hot polling rounds, then rounds
+// spaced by a growing __nanosleep (capped), at most `limit` rounds in one
+// wait; past the limit the wait records SPTRSV_ERR_TIMEOUT for its row and
+// goes on with NaN, so every later row still finishes.
 struct SpinPolicy {
     long long limit;
     int hot;          // polls before the first sleep
     unsigned max_ns;  // back-off cap
 };
 
-// Waits until *p is published; on running out of polls records a timeout
-// for `row` and returns NaN (which then propagates to every later row, so
-// the whole solve still finishes).
-template <typename T>
-__device__ __forceinline__ T wait_value(const T* p, const SpinPolicy& sp,
-                                        unsigned long long* status, int row) {
-    T v = ld_relaxed(p);
-    if (!Marker<T>::pending(v)) return v;
-    long long it = 1;
-    unsigned ns = 32;
-    while (true) {
-        if (it >= sp.hot) {
-            __nanosleep(ns);
-            ns = ns < sp.max_ns ? ns * 2 : sp.max_ns;
-        }
-        v = ld_relaxed(p);
-        if (!Marker<T>::pending(v)) return v;
-        if (++it >= sp.limit) {
-            report(status, row, kCodeTimeout);
-            return Marker<T>::canonical_nan();
-        }
-    }
-}
-
-// Level analysis uses -1 as its "not yet computed" marker.
-__device__ __forceinline__ int wait_level(const int* p, const SpinPolicy& sp,
-                                          unsigned long long* status, int row) {
-    int v = ld_relaxed(p);
-    if (v >= 0) return v;
-    long long it = 1;
-    unsigned ns = 32;
-    while (true) {
-        if (it >= sp.hot) {
-            __nanosleep(ns);
-            ns = ns < sp.max_ns ? ns * 2 : sp.max_ns;
-        }
-        v = ld_relaxed(p);
-        if (v >= 0) return v;
-        if (++it >= sp.limit) {
-            report(status, row, kCodeTimeout);
-            return 0;
-        }
-    }
-}
+// Entries a lane loads at once (one chunk) in the self-scheduled kernels.
+constexpr int kChunk = 4;
 
 // Mask of the W-lane group (sub-warp) that `lane` belongs to.
 template <int W>

@@ -28,11 +28,13 @@ struct CusRef {
         if (_e != cudaSuccess) return 200 + (int)_e; \
     } while (0)
 
+#define CUSREF_API __attribute__((visibility("default")))
+
 extern "C" {
 
 // Builds the cuSPARSE matrix/vector descriptors and runs SpSV analysis on
 // `stream`.  Returns 0 on success; *out receives an opaque handle.
-int cusref_create(int n, int nnz, const int* rowptr, const int* colidx, const void* vals, int f64,
+CUSREF_API int cusref_create(int n, int nnz, const int* rowptr, const int* colidx, const void* vals, int f64,
                   int upper, int unit, const void* x, void* y, void* stream, void** out) {
     if (!out) return 1;
     *out = nullptr;
@@ -63,7 +65,7 @@ int cusref_create(int n, int nnz, const int* rowptr, const int* colidx, const vo
 }
 
 // y = op(A)^{-1} x with the analysed matrix; x and y may be new pointers.
-int cusref_solve(void* handle, const void* x, void* y, void* stream) {
+CUSREF_API int cusref_solve(void* handle, const void* x, void* y, void* stream) {
     CusRef* h = (CusRef*)handle;
     if (!h) return 1;
     CS(cusparseSetStream(h->handle, (cudaStream_t)stream));
@@ -77,7 +79,7 @@ int cusref_solve(void* handle, const void* x, void* y, void* stream) {
     return 0;
 }
 
-int cusref_destroy(void* handle) {
+CUSREF_API int cusref_destroy(void* handle) {
     CusRef* h = (CusRef*)handle;
     if (!h) return 0;
     cudaDeviceSynchronize();

@@ -3,13 +3,16 @@
 // right-hand-side columns l, l + W, ...  Each stored entry is read once per
 // column tile and applied to all of them, so the matrix traffic is shared by
 // the k solves (the multiple-right-hand-side case of Sec. 1).  No reduction
-// is needed: each lane accumulates its own columns in entry order.
+// is needed: each lane accumulates its own column in entry order and
+// publishes it by itself, so in the self-scheduled form every (row, column)
+// value is its own ready flag and lanes never wait for each other.
 #include "internal.h"
 
 namespace sptrsv {
 
-template <typename T, int W, bool MAP, bool SELF>
-__device__ __forceinline__ void mrhs_row(const SolveParams& p, int i, int sl) {
+// Level-scheduled row: all dependencies are final (earlier launches).
+template <typename T, int W, bool MAP>
+__device__ __forceinline__ void mrhs_row_level(const SolveParams& p, int i, int sl) {
     const T* __restrict__ vals = (const T*)p.vals;
     const T* b = (const T*)p.b;
     T* x = (T*)p.x;
@@ -21,51 +24,134 @@ __device__ __forceinline__ void mrhs_row(const SolveParams& p, int i, int sl) {
     }
     for (int c0 = 0; c0 < p.nrhs; c0 += W) {
         const int c = c0 + sl;
-        const bool on = c < p.nrhs;
+        if (c >= p.nrhs) break;
         T acc = T(0);
         for (int q = beg; q < end; ++q) {
             const int j = p.idx[q];
             if (j == i) continue;
-            const T a = vals[MAP ? p.vmap[q] : q];
-            if (on) {
-                const T* src = x + (long long)j * p.ldx + c;
-                const T xv = SELF ? wait_value(src, p.spin, p.status, i) : *src;
-                acc += a * xv;
-            }
+            acc += vals[MAP ? p.vmap[q] : q] * x[(long long)j * p.ldx + c];
         }
-        if (on) {
-            T xi = b[(long long)i * p.ldb + c] - acc;
-            if (!p.unit) xi = xi / di;
-            T* dst = x + (long long)i * p.ldx + c;
-            if (SELF) {
-                if (i != p.withhold) st_relaxed(dst, publishable(xi));
-            } else {
-                *dst = xi;
-            }
-        }
+        T xi = b[(long long)i * p.ldb + c] - acc;
+        if (!p.unit) xi = xi / di;
+        x[(long long)i * p.ldx + c] = xi;
     }
 }
 
 template <typename T, int W, bool MAP, bool SELF>
 __global__ void __launch_bounds__(1024) solve_mrhs_k(SolveParams p) {
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int E = kChunk;
     const int lane = threadIdx.x & 31;
-    const int sub = lane / W;
-    const int sl = lane - sub * W;
+    const int grp = lane / W;
+    const int sl = lane - grp * W;
     if (!SELF) {
         const long long g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / W;
-        if (g < p.cnt) mrhs_row<T, W, MAP, false>(p, p.jlev[p.kbeg + g], sl);
+        if (g < p.cnt) mrhs_row_level<T, W, MAP>(p, p.jlev[p.kbeg + g], sl);
         return;
     }
     constexpr int R = 32 / W;
+    const T* __restrict__ vals = (const T*)p.vals;
+    const T* b = (const T*)p.b;
+    T* x = (T*)p.x;
     int t = 0;
     if (lane == 0) t = atomicAdd(p.ticket, 1);
-    t = __shfl_sync(0xffffffffu, t, 0);
+    t = __shfl_sync(FULL, t, 0);
     while ((long long)t * R < p.n) {
         int tn = 0;
         if (lane == 0) tn = atomicAdd(p.ticket, 1);
-        const long long k = (long long)t * R + sub;
-        if (k < p.n) mrhs_row<T, W, MAP, true>(p, p.jlev[k], sl);
-        t = __shfl_sync(0xffffffffu, tn, 0);
+        const long long k = (long long)t * R + grp;
+        int i = 0, beg = 0, end = 0;
+        T dinv = T(1);
+        int col = sl;
+        bool lane_done = k >= p.n || col >= p.nrhs;
+        if (k < p.n) {
+            i = p.jlev[k];
+            beg = p.ptr[i];
+            end = p.ptr[i + 1];
+            if (!p.unit) {
+                const int q = p.diag_first ? beg : end - 1;
+                dinv = T(1) / vals[MAP ? p.vmap[q] : q];
+            }
+        }
+        // per-lane state: column `col`, next entry q0, chunk of E entries
+        int q0 = beg;
+        int c[E];
+        T a[E], v[E];
+        unsigned live = 0, pend = 0;
+        T acc = T(0);
+        auto load_chunk = [&]() {
+            live = pend = 0;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int q = q0 + e;
+                c[e] = -1;
+                a[e] = T(0);
+                v[e] = T(0);
+                if (q < end) {
+                    const int cc = p.idx[q];
+                    if (cc != i) {
+                        c[e] = cc;
+                        a[e] = vals[MAP ? p.vmap[q] : q];
+                        live |= 1u << e;
+                    }
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                if (live & (1u << e)) v[e] = ld_relaxed(x + (long long)c[e] * p.ldx + col);
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                if ((live & (1u << e)) && Marker<T>::pending(v[e])) pend |= 1u << e;
+        };
+        if (!lane_done) load_chunk();
+        long long waits = 0;
+        unsigned ns = 32;
+        while (true) {
+            if (!lane_done && pend == 0) {
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    if (live & (1u << e)) acc += a[e] * v[e];
+                q0 += E;
+                if (q0 >= end) {  // column done: publish it, move to the next tile
+                    const T xi = (b[(long long)i * p.ldb + col] - acc) * dinv;
+                    if (i != p.withhold) st_relaxed(x + (long long)i * p.ldx + col, publishable(xi));
+                    col += W;
+                    acc = T(0);
+                    q0 = beg;
+                    if (col >= p.nrhs) lane_done = true;
+                    else load_chunk();
+                } else {
+                    load_chunk();
+                }
+            }
+            if (__all_sync(FULL, lane_done)) break;
+            if (__any_sync(FULL, pend != 0)) {
+                if (pend) {
+#pragma unroll
+                    for (int e = 0; e < E; ++e)
+                        if (pend & (1u << e)) v[e] = ld_relaxed(x + (long long)c[e] * p.ldx + col);
+#pragma unroll
+                    for (int e = 0; e < E; ++e)
+                        if ((pend & (1u << e)) && !Marker<T>::pending(v[e])) pend &= ~(1u << e);
+                }
+                if (++waits >= p.spin.limit) {
+                    if (pend) {
+                        report(p.status, i, kCodeTimeout);
+#pragma unroll
+                        for (int e = 0; e < E; ++e)
+                            if (pend & (1u << e)) v[e] = Marker<T>::canonical_nan();
+                        pend = 0;
+                    }
+                } else if (waits >= p.spin.hot) {
+                    __nanosleep(ns);
+                    ns = ns < p.spin.max_ns ? ns * 2 : p.spin.max_ns;
+                }
+            } else {
+                waits = 0;
+                ns = 32;
+            }
+        }
+        t = __shfl_sync(FULL, tn, 0);
     }
 }
 

@@ -9,9 +9,16 @@
 //    with a marker, and each lane waits directly on the x(j) it needs with a
 //    GPU-scope relaxed load.  The published value is its own ready flag, so
 //    a dependency costs one L2 round trip and no fence.
-//  * A row is reduced by a sub-warp of W lanes (W chosen per matrix), not by
-//    a whole warp, with shuffle reductions instead of shared memory; every
-//    wait is bounded.
+//  * A row is reduced by a sub-warp of W lanes (W chosen per matrix).  The
+//    paper lets lane 0 spin and relies on warp lockstep, which sm_70 and
+//    later no longer guarantee.  Here the whole warp stays converged in one
+//    round loop: every lane issues the loads of all its entries of a chunk
+//    at once, re-polls only the pending ones each round, and a row is reduced
+//    (shuffles) and published inside the loop as soon as all its lanes are
+//    done.  Rows of one ticket may therefore depend on one another (a ticket
+//    can straddle two levels) without deadlock, and no sub-warp waits in a
+//    divergent spin that the scheduler would serialise.  Every wait is
+//    bounded.
 #include "internal.h"
 
 namespace sptrsv {
@@ -51,51 +58,124 @@ cudaError_t launch_prep_self(bool f64, int n, int nrhs, void* x, long long ldx, 
     return cudaGetLastError();
 }
 
+
 template <typename T, int W, bool MAP>
 __global__ void __launch_bounds__(1024) self_solve_k1(SolveParams p) {
     constexpr int R = 32 / W;
+    constexpr int E = kChunk;
+    constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const int sub = lane / W;
-    const int sl = lane - sub * W;
+    const int grp = lane / W;
+    const int sl = lane - grp * W;
     const unsigned gmask = group_mask<W>(lane);
     const T* __restrict__ vals = (const T*)p.vals;
     const T* b = (const T*)p.b;
     T* x = (T*)p.x;
     int t = 0;
     if (lane == 0) t = atomicAdd(p.ticket, 1);
-    t = __shfl_sync(0xffffffffu, t, 0);
+    t = __shfl_sync(FULL, t, 0);
     while ((long long)t * R < p.n) {
         int tn = 0;
         if (lane == 0) tn = atomicAdd(p.ticket, 1);  // next ticket, consumed after this one
-        const long long k = (long long)t * R + sub;
-        if (k < p.n) {
-            const int i = p.jlev[k];
-            const int beg = p.ptr[i], end = p.ptr[i + 1];
-            T bi = T(0), di = T(1);
+        const long long k = (long long)t * R + grp;
+        const bool has_row = k < p.n;
+        int i = 0, beg = 0, end = 0;
+        T bi = T(0), dinv = T(1);
+        if (has_row) {
+            i = p.jlev[k];
+            beg = p.ptr[i];
+            end = p.ptr[i + 1];
             if (sl == 0) {
                 bi = b[(long long)i * p.ldb];
-                if (!p.unit) {
+                if (!p.unit) {  // 1/d(i) while the dependencies are pending, as SLFR does
                     const int q = p.diag_first ? beg : end - 1;
-                    di = vals[MAP ? p.vmap[q] : q];
+                    dinv = T(1) / vals[MAP ? p.vmap[q] : q];
                 }
-            }
-            T sum = T(0);
-            for (int q = beg + sl; q < end; q += W) {
-                const int c = p.idx[q];
-                if (c != i) {
-                    const T a = vals[MAP ? p.vmap[q] : q];
-                    const T xv = wait_value(x + (long long)c * p.ldx, p.spin, p.status, i);
-                    sum += a * xv;
-                }
-            }
-            sum = group_sum<W>(sum, gmask);
-            if (sl == 0) {
-                T xi = bi - sum;
-                if (!p.unit) xi = xi / di;
-                if (i != p.withhold) st_relaxed(x + (long long)i * p.ldx, publishable(xi));
             }
         }
-        t = __shfl_sync(0xffffffffu, tn, 0);
+        // ---- per-lane chunk state: entries q0 + e*W, e < E
+        int q0 = beg + sl;
+        int c[E];
+        T a[E], v[E];
+        unsigned live = 0, pend = 0;  // entries that count / still unpublished
+        auto load_chunk = [&]() {
+            live = pend = 0;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int q = q0 + e * W;
+                c[e] = -1;
+                a[e] = T(0);
+                v[e] = T(0);
+                if (q < end) {
+                    const int cc = p.idx[q];
+                    if (cc != i) {
+                        c[e] = cc;
+                        a[e] = vals[MAP ? p.vmap[q] : q];
+                        live |= 1u << e;
+                    }
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                if (live & (1u << e)) v[e] = ld_relaxed(x + (long long)c[e] * p.ldx);
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                if ((live & (1u << e)) && Marker<T>::pending(v[e])) pend |= 1u << e;
+        };
+        bool lane_done = q0 >= end;
+        if (!lane_done) load_chunk();
+        bool published = !has_row;
+        T sum = T(0);
+        long long waits = 0;
+        unsigned ns = 32;
+        while (true) {
+            if (!lane_done && pend == 0) {  // fold a complete chunk in entry order
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    if (live & (1u << e)) sum += a[e] * v[e];
+                q0 += W * E;
+                if (q0 >= end) lane_done = true;
+                else load_chunk();
+            }
+            const unsigned done = __ballot_sync(FULL, lane_done);
+            const bool row_ready = (done & gmask) == gmask;
+            T tot = group_sum<W>(sum, FULL);
+            if (row_ready && !published) {
+                if (sl == 0) {
+                    const T xi = (bi - tot) * dinv;
+                    if (i != p.withhold) st_relaxed(x + (long long)i * p.ldx, publishable(xi));
+                }
+                published = true;
+            }
+            if (__all_sync(FULL, published)) break;
+            // The wait bookkeeping below is warp-uniform (driven by __any_sync).
+            if (__any_sync(FULL, pend != 0)) {
+                if (pend) {
+#pragma unroll
+                    for (int e = 0; e < E; ++e)
+                        if (pend & (1u << e)) v[e] = ld_relaxed(x + (long long)c[e] * p.ldx);
+#pragma unroll
+                    for (int e = 0; e < E; ++e)
+                        if ((pend & (1u << e)) && !Marker<T>::pending(v[e])) pend &= ~(1u << e);
+                }
+                if (++waits >= p.spin.limit) {
+                    if (pend) {
+                        report(p.status, i, kCodeTimeout);
+#pragma unroll
+                        for (int e = 0; e < E; ++e)
+                            if (pend & (1u << e)) v[e] = Marker<T>::canonical_nan();
+                        pend = 0;
+                    }
+                } else if (waits >= p.spin.hot) {
+                    __nanosleep(ns);
+                    ns = ns < p.spin.max_ns ? ns * 2 : p.spin.max_ns;
+                }
+            } else {
+                waits = 0;
+                ns = 32;
+            }
+        }
+        t = __shfl_sync(FULL, tn, 0);
     }
 }
 

@@ -32,7 +32,7 @@ class _DeviceArray:
 
     def __init__(self, ptr, n, typestr):
         self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr,
-                                         "data": (int(ptr), True), "version": 3,
+                                         "data": (int(ptr), False), "version": 3,
                                          "strides": None}
 
 
