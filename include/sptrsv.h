@@ -260,6 +260,45 @@ SPTRSV_API sptrsv_status_t sptrsv_profile_read(sptrsv_plan_t plan, double *total
  * accounting). */
 SPTRSV_API int sptrsv_last_launch_count(sptrsv_plan_t plan);
 
+/* ------------------------------------------------------------ no allocation */
+
+/* Largest n that sptrsv_solve_noalloc accepts.  Its working memory is one
+ * fixed array inside the library: 256 bytes plus 4 bytes per row, i.e.
+ * 16 MiB + 256 B, held on every GPU that loads the library until exit. */
+#define SPTRSV_NOALLOC_MAX_ROWS 4194304
+
+/* Solves A x = b for one right-hand side without a plan and without any
+ * device allocation (the paper has no counterpart to this call).  It is for
+ * callers that may not call cudaMalloc or cudaFree: code running inside an
+ * application that owns all device memory through its own pool, or a
+ * latency-critical loop that must not touch the device allocator (which can
+ * take global locks and synchronise the device).  Such callers cannot make a
+ * plan either, since the analysis allocates its level sets.
+ *
+ * What it does, all enqueued on `stream`: clears its working memory,
+ * validates the CSR as sptrsv_analyze does, then runs a self-scheduled solve
+ * in substitution order (rows wait for per-row ready flags; no level sets).
+ *   n, nnz, d_rowptr, d_colidx, d_vals, dtype, uplo, diag: as sptrsv_analyze
+ *   d_b, d_x   device vectors of n elements, contiguous; d_x == d_b allowed
+ *   error_row  NULL: return right after enqueueing (device-side errors are
+ *              then not reported).  Non-NULL: wait for `stream`, then return
+ *              the device-side result -- SPTRSV_ERR_STRUCTURE or
+ *              SPTRSV_ERR_ZERO_PIVOT from validation (x untouched) or
+ *              SPTRSV_ERR_TIMEOUT -- with its row in *error_row (-1 if none).
+ * Returns SPTRSV_ERR_INVALID_ARG for n > SPTRSV_NOALLOC_MAX_ROWS.
+ * Working memory: one array declared at file scope in the library, shared by
+ * every call; each call clears the parts it uses before reading them, and
+ * the array keeps the last call's contents afterwards.  Calls whose GPU work
+ * overlaps (other streams, other host threads) race on it: serialise them.
+ * The first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress (that device current); make that first call before
+ * any stream capture. */
+SPTRSV_API sptrsv_status_t sptrsv_solve_noalloc(int n, int nnz, const int *d_rowptr,
+                                                const int *d_colidx, const void *d_vals,
+                                                sptrsv_dtype_t dtype, sptrsv_uplo_t uplo,
+                                                sptrsv_diag_t diag, const void *d_b,
+                                                void *d_x, void *stream, int *error_row);
+
 /* Test hook: the self-scheduled solve skips publishing this row (-1 = off),
  * so that every row depending on it exercises the bounded wait and the
  * SPTRSV_ERR_TIMEOUT path.  Faults nothing: the waits end at the limit. */

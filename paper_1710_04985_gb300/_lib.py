@@ -56,7 +56,11 @@ SIGNATURES = [
     ("sptrsv_profile_read", _c_int, [_vp, _dp, _ip]),
     ("sptrsv_last_launch_count", _c_int, [_vp]),
     ("sptrsv_debug_withhold_row", _c_int, [_vp, _c_int]),
+    ("sptrsv_solve_noalloc", _c_int, [_c_int, _c_int, _vp, _vp, _vp, _c_int, _c_int, _c_int,
+                                      _vp, _vp, _vp, _ip]),
 ]
+
+NOALLOC_MAX_ROWS = 4194304
 
 _lib = None
 
