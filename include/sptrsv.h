@@ -81,7 +81,12 @@ typedef enum { SPTRSV_LOWER = 0, SPTRSV_UPPER = 1 } sptrsv_uplo_t;
 typedef enum { SPTRSV_NON_UNIT = 0, SPTRSV_UNIT = 1 } sptrsv_diag_t;
 typedef enum {
     SPTRSV_ALGO_LEVEL = 0,        /* Alg. 1 (LEVR): one launch per level                 */
-    SPTRSV_ALGO_SELF = 1          /* Alg. 3 (SLFR): one launch, rows self-scheduled      */
+    SPTRSV_ALGO_SELF = 1,         /* Alg. 3 (SLFR): one launch, rows self-scheduled in
+                                     level order                                         */
+    SPTRSV_ALGO_SELF_TILED = 2    /* Alg. 3 over tiles of consecutive rows: a block owns a
+                                     tile and serves in-tile dependencies from shared
+                                     memory (Sec. 4.3 remark 2); one right-hand side,
+                                     more columns fall back to SPTRSV_ALGO_SELF          */
 } sptrsv_algo_t;
 
 /* ------------------------------------------------------------------ setup */
@@ -202,6 +207,15 @@ SPTRSV_API sptrsv_status_t sptrsv_set_tuning(sptrsv_plan_t plan, int lanes_per_r
                                   int block_size, int max_blocks);
 SPTRSV_API sptrsv_status_t sptrsv_get_tuning(sptrsv_plan_t plan, int *lanes_per_row,
                                   int *block_size, int *max_blocks);
+
+/* Tiles of SPTRSV_ALGO_SELF_TILED: tile_rows consecutive positions of the
+ * substitution order (level_order = 0: natural row order, reversed for an
+ * upper plan; suits banded and chain-like matrices) or of the level order
+ * jlev (level_order = 1: a tile spans many consecutive narrow levels).
+ * 32 <= tile_rows, tile_rows * element size <= 48 KB - 256 B (6112 rows in
+ * FP64, 12224 in FP32).  Default 2048 rows, substitution order. */
+SPTRSV_API sptrsv_status_t sptrsv_set_tiling(sptrsv_plan_t plan, int tile_rows,
+                                             int level_order);
 
 /* Upper bound on the polling rounds of one dependency wait before the wait
  * gives up, records SPTRSV_ERR_TIMEOUT with its row and goes on with NaN so

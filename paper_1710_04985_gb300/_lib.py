@@ -24,7 +24,7 @@ ERR_INTERNAL = 8
 F64, F32 = 0, 1
 LOWER, UPPER = 0, 1
 NON_UNIT, UNIT = 0, 1
-ALGO_LEVEL, ALGO_SELF = 0, 1
+ALGO_LEVEL, ALGO_SELF, ALGO_SELF_TILED = 0, 1, 2
 
 # (name, restype, argtypes) for every entry point of include/sptrsv.h
 _c_int, _c_ll, _c_dbl = ctypes.c_int, ctypes.c_longlong, ctypes.c_double
@@ -45,6 +45,7 @@ SIGNATURES = [
     ("sptrsv_set_tuning", _c_int, [_vp, _c_int, _c_int, _c_int]),
     ("sptrsv_get_tuning", _c_int, [_vp, _ip, _ip, _ip]),
     ("sptrsv_set_spin_limit", _c_int, [_vp, _c_ll]),
+    ("sptrsv_set_tiling", _c_int, [_vp, _c_int, _c_int]),
     ("sptrsv_levels", _c_int, [_vp, _c_int, _ip, _pp, _pp, _pp]),
     ("sptrsv_transpose_pattern", _c_int, [_vp, _pp, _pp, _pp]),
     ("sptrsv_status", _c_int, [_vp, _vp, _ip]),

@@ -1,12 +1,14 @@
 """Launch-shape autotuner for the solve kernels.
 
-Times the self-scheduled (or level-scheduled) solve of a plan with CUDA
-events on the current stream and keeps the fastest shape.  Two stages:
-first the sub-warp width (lanes per row, hence rows per warp = 32 / lanes)
-at the default block size, then, for that width, the block size and the cap
-on the persistent grid (how many warps wait ahead of the dependency frontier:
-more hides latency, fewer polls less L2 traffic).  Results are cached per
-matrix signature for the process.
+Times the solves of a plan with CUDA events on the current stream and keeps
+the fastest shape.  ``tune`` searches one algorithm in two stages: first the
+sub-warp width (lanes per row, hence rows per warp = 32 / lanes) at the
+default block size, then, for that width, the block size and the cap on the
+persistent grid (how many warps wait ahead of the dependency frontier: more
+hides latency, fewer polls less L2 traffic), and for the tiled form the tile
+size.  ``tune_algos`` runs ``tune`` for the level-ordered and the tiled
+self-scheduled forms and keeps the faster, recording it on the plan.
+Results are cached per matrix signature for the process.
 """
 from __future__ import annotations
 
@@ -19,6 +21,8 @@ _CACHE: dict = {}
 LANES = (1, 2, 4, 8, 16, 32)
 BLOCKS = (128, 256, 512)
 GRID_FRACTIONS = (0, 4, 2, 1)      # max_blocks = fraction * SMs (0: as many as fit)
+TILES = (1024, 2048, 4096)
+TILE_ORDERS = (False, True)      # substitution order, level order
 
 
 def signature(plan, nrhs, algo):
@@ -43,39 +47,74 @@ def time_solve(plan, b, x, algo="self", reps=3, transpose=False):
 
 
 def tune(plan, b, x=None, algo="self", lanes=LANES, blocks=BLOCKS, grids=GRID_FRACTIONS,
-         reps=3, use_cache=True, transpose=False):
-    """Pick lanes-per-row, block size and grid cap for `plan` on `b`.
+         tiles=TILES, reps=3, use_cache=True, transpose=False, tile_orders=TILE_ORDERS):
+    """Pick lanes-per-row, block size, grid cap (and tile size for "tiled")
+    for `plan` on `b`.
 
     Sets the winner on the plan and returns ``{"best": (lanes, block,
-    max_blocks, ms), "table": [(lanes, block, max_blocks, ms), ...]}``."""
+    max_blocks, ms, tile_rows, level_order), "table": [...]}``."""
     nrhs = 1 if b.dim() == 1 else b.shape[1]
-    key = signature(plan, nrhs, algo) + (transpose, tuple(lanes), tuple(blocks), tuple(grids))
+    key = signature(plan, nrhs, algo) + (transpose, tuple(lanes), tuple(blocks), tuple(grids),
+                                         tuple(tiles), tuple(tile_orders))
     if use_cache and key in _CACHE:
         best = _CACHE[key]["best"]
-        plan.set_tuning(best[0], best[1], best[2])
+        _apply(plan, best, algo)
         return _CACHE[key]
     if x is None:
         x = torch.empty_like(b)
     sms = torch.cuda.get_device_properties(b.device).multi_processor_count
+    esize = 8 if plan.dtype == torch.float64 else 4
     table = []
 
-    def run(w, blk, mb):
+    def run(w, blk, mb, tile, order):
         plan.set_tuning(w, blk, mb)
+        if algo == "tiled":
+            plan.set_tiling(tile, order)
         ms = time_solve(plan, b, x, algo, reps, transpose)
-        table.append((w, blk, mb, ms))
+        table.append((w, blk, mb, ms, tile, order))
         return ms
 
     default_block = 256 if 256 in blocks else blocks[0]
-    for w in lanes:
-        run(w, default_block, 0)
-    w_best = min(table, key=lambda r: r[3])[0]
-    if algo == "self":
+    tile0 = 2048 if 2048 in tiles else tiles[0]
+    first_grid = 2 * sms if algo == "tiled" else 0
+    orders = tile_orders if algo == "tiled" else (False,)
+    for order in orders:
+        for w in lanes:
+            run(w, default_block, first_grid, tile0, order)
+    w_best, order_best = min(table, key=lambda r: r[3])[0], min(table, key=lambda r: r[3])[5]
+    if algo in ("self", "tiled"):
         for blk in blocks:
             for frac in grids:
-                if (blk, frac) != (default_block, 0):
-                    run(w_best, blk, frac * sms)
+                if (blk, frac * sms) != (default_block, first_grid):
+                    run(w_best, blk, frac * sms, tile0, order_best)
+    if algo == "tiled":
+        bb = min(table, key=lambda r: r[3])
+        for tile in tiles:
+            if tile != tile0 and tile * esize <= 48 * 1024 - 256:
+                run(bb[0], bb[1], bb[2], tile, bb[5])
     best = min(table, key=lambda r: r[3])
-    plan.set_tuning(best[0], best[1], best[2])
+    _apply(plan, best, algo)
     result = {"best": best, "table": table}
     _CACHE[key] = result
     return result
+
+
+def _apply(plan, best, algo):
+    plan.set_tuning(best[0], best[1], best[2])
+    if algo == "tiled":
+        plan.set_tiling(best[4], best[5])
+
+
+def tune_algos(plan, b, x=None, algos=("self", "tiled"), reps=3, use_cache=True, **kw):
+    """Tune each self-scheduled form and keep the faster one.
+
+    Returns ``{"algo": name, "best": ..., "per_algo": {name: tune(...)}}`` and
+    sets ``plan.best_algo`` (used by ``plan.solve(..., algo="auto")``)."""
+    nrhs = 1 if b.dim() == 1 else b.shape[1]
+    if nrhs > 1:
+        algos = tuple(a for a in algos if a != "tiled") or ("self",)
+    per = {a: tune(plan, b, x, algo=a, reps=reps, use_cache=use_cache, **kw) for a in algos}
+    name = min(per, key=lambda a: per[a]["best"][3])
+    _apply(plan, per[name]["best"], name)
+    plan.best_algo = name
+    return {"algo": name, "best": per[name]["best"], "per_algo": per}

@@ -58,7 +58,7 @@ class BatchedTriangularSolve:
         self.tuning = None
         if tune:
             self.b.uniform_(-1, 1)
-            self.tuning = autotune.tune(self.plan, self.b, self.x)
+            self.tuning = autotune.tune_algos(self.plan, self.b, self.x)
         self.graph = None
 
     @property
@@ -67,11 +67,11 @@ class BatchedTriangularSolve:
 
     def capture(self):
         """Record the solve of self.b into self.x as a CUDA graph."""
-        self.plan.solve(self.b, out=self.x)          # warm-up outside capture
+        self.plan.solve(self.b, out=self.x, algo="auto")   # warm-up outside capture
         torch.cuda.synchronize()
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
-            self.plan.solve(self.b, out=self.x)
+            self.plan.solve(self.b, out=self.x, algo="auto")
         self.graph = g
         return g
 

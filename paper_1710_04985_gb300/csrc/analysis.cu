@@ -477,6 +477,22 @@ cudaError_t launch_gather(const int* src, int src_len, const int* index, int m, 
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------ inverse permutation
+// ipos[jlev[k]] = k: the position of every row in level order.
+__global__ void inverse_perm_k(const int* __restrict__ perm, int n, int* ipos) {
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x)
+        ipos[perm[k]] = (int)k;
+}
+
+cudaError_t launch_inverse_perm(const int* perm, int n, int* ipos, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    long long g = ((long long)n + 255) / 256;
+    if (g > 4096) g = 4096;
+    inverse_perm_k<<<(int)g, 256, 0, s>>>(perm, n, ipos);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ level-set check
 __global__ void verify_levels_k(int n, int nlev, const int* __restrict__ lev,
                                 const int* __restrict__ ilev, const int* __restrict__ jlev,

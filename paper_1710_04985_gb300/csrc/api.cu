@@ -39,6 +39,7 @@ struct Levels {
     int* lev = nullptr;
     int* ilev = nullptr;
     int* jlev = nullptr;
+    int* ipos = nullptr;  // inverse of jlev (level-order tiles)
     std::vector<int> h_ilev;
 };
 
@@ -119,6 +120,8 @@ struct sptrsv_plan_s {
     size_t rd_elems = 0;
     unsigned long long* stats = nullptr;  // [0] max|r| [1] |A|_inf [2] max|x| [3] max|b|
     int lanes = 4, block = 256, max_blocks = 0;
+    int tile_rows = 2048;
+    bool tile_level_order = false;
     SpinPolicy spin{1ll << 24, 256, 128};
     int withhold = -1;
     double analysis_ms = 0.0;
@@ -134,6 +137,7 @@ void free_levels(Levels& L) {
     cudaFree(L.lev);
     cudaFree(L.ilev);
     cudaFree(L.jlev);
+    cudaFree(L.ipos);
     L = Levels();
 }
 
@@ -203,6 +207,7 @@ sptrsv_status_t build_levels(sptrsv_plan_t P, const int* ptr, const int* idx, bo
     L.nlev = nlev;
     CK(cudaMalloc(&L.ilev, sizeof(int) * (size_t)(nlev + 1)));
     CK(cudaMalloc(&L.jlev, sizeof(int) * (size_t)n));
+    CK(cudaMalloc(&L.ipos, sizeof(int) * (size_t)n));
     int* count = nullptr;
     int* scratch = nullptr;
     const int hist_n = radix_hist_entries(n);
@@ -232,6 +237,12 @@ sptrsv_status_t build_levels(sptrsv_plan_t P, const int* ptr, const int* idx, bo
     if (e != cudaSuccess) rc = cuda_fail(e);
     cudaFree(scratch);
     if (rc == SPTRSV_OK) rc = take_status(P, s, &row);
+    // jlev is now known to be a permutation: invert it for level-order tiles.
+    if (rc == SPTRSV_OK) {
+        e = launch_inverse_perm(L.jlev, n, L.ipos, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_fail(e);
+    }
     return rc;
 }
 
@@ -338,6 +349,7 @@ sptrsv_status_t run_solve(sptrsv_plan_t P, bool trans, bool f64, const void* val
     p.status = P->status;
     p.spin = P->spin;
     p.withhold = P->withhold;
+    p.ipos = (algo == SPTRSV_ALGO_SELF_TILED && P->tile_level_order) ? L.ipos : nullptr;
     const bool mrhs = nrhs > 1;
     const int lanes = mrhs ? mrhs_lanes(nrhs) : P->lanes;
     int launches = 0;
@@ -370,10 +382,22 @@ sptrsv_status_t run_solve(sptrsv_plan_t P, bool trans, bool f64, const void* val
         if (P->max_blocks > 0 && grid > P->max_blocks) grid = P->max_blocks;
         if (grid > want_blocks) grid = want_blocks;
         if (grid < 1) grid = 1;
-        ST(prof_begin(P, s));
-        CK(mrhs ? launch_mrhs(f64, lanes, true, p, (int)grid, P->block, s)
-                : launch_self_k1(f64, lanes, p, (int)grid, P->block, s));
-        ST(prof_end(P, s));
+        if (algo == SPTRSV_ALGO_SELF_TILED && !mrhs) {
+            const long long tiles = ((long long)P->n + P->tile_rows - 1) / P->tile_rows;
+            grid = (long long)tiled_blocks_per_sm(f64, lanes, trans, P->block, P->tile_rows) *
+                   P->num_sms;
+            if (P->max_blocks > 0 && grid > P->max_blocks) grid = P->max_blocks;
+            if (grid > tiles) grid = tiles;
+            if (grid < 1) grid = 1;
+            ST(prof_begin(P, s));
+            CK(launch_tiled_k1(f64, lanes, p, P->tile_rows, (int)grid, P->block, s));
+            ST(prof_end(P, s));
+        } else {
+            ST(prof_begin(P, s));
+            CK(mrhs ? launch_mrhs(f64, lanes, true, p, (int)grid, P->block, s)
+                    : launch_self_k1(f64, lanes, p, (int)grid, P->block, s));
+            ST(prof_end(P, s));
+        }
         launches = 2;
     }
     P->last_launches = launches;
@@ -382,7 +406,8 @@ sptrsv_status_t run_solve(sptrsv_plan_t P, bool trans, bool f64, const void* val
 
 sptrsv_status_t solve_common(sptrsv_plan_t P, bool trans, const void* b, void* x, int nrhs,
                              int ld, sptrsv_algo_t algo, void* stream) {
-    if (!P || nrhs < 1 || ld < nrhs || (algo != SPTRSV_ALGO_LEVEL && algo != SPTRSV_ALGO_SELF))
+    if (!P || nrhs < 1 || ld < nrhs ||
+        (algo != SPTRSV_ALGO_LEVEL && algo != SPTRSV_ALGO_SELF && algo != SPTRSV_ALGO_SELF_TILED))
         return SPTRSV_ERR_INVALID_ARG;
     P->last_launches = 0;
     if (P->n == 0) return SPTRSV_OK;
@@ -619,6 +644,16 @@ sptrsv_status_t sptrsv_get_tuning(sptrsv_plan_t plan, int* lanes_per_row, int* b
     if (lanes_per_row) *lanes_per_row = plan->lanes;
     if (block_size) *block_size = plan->block;
     if (max_blocks) *max_blocks = plan->max_blocks;
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t sptrsv_set_tiling(sptrsv_plan_t plan, int tile_rows, int level_order) {
+    if (!plan || tile_rows < 32 || (level_order != 0 && level_order != 1))
+        return SPTRSV_ERR_INVALID_ARG;
+    const size_t esize = plan->f64 ? sizeof(double) : sizeof(float);
+    if (esize * (size_t)tile_rows > 48 * 1024 - 256) return SPTRSV_ERR_INVALID_ARG;
+    plan->tile_rows = tile_rows;
+    plan->tile_level_order = level_order != 0;
     return SPTRSV_OK;
 }
 

@@ -28,6 +28,8 @@ struct SolveParams {
     unsigned long long* status;
     SpinPolicy spin;
     int withhold;         // test hook: row whose result is never published (-1: none)
+    const int* ipos;      // tiled solve in level order: position of each row in jlev
+                          // (nullptr: tiles follow the substitution order)
     int kbeg, cnt;        // level-scheduled: this launch's slice of jlev
 };
 
@@ -42,6 +44,12 @@ cudaError_t launch_mrhs(bool f64, int lanes, bool self, const SolveParams& p, in
                         cudaStream_t s);
 // Resident blocks per SM of the kernel a launch with these choices would use.
 int self_blocks_per_sm(bool f64, int lanes, bool mrhs, bool map, int block);
+// Tiled self-scheduled solve (solve_tiled.cu): tiles of `tile_rows`
+// consecutive positions of the substitution order (p.ipos == nullptr) or of
+// the level order jlev (p.ipos != nullptr); tile_rows * sizeof(T) <= 48 KB.
+cudaError_t launch_tiled_k1(bool f64, int lanes, const SolveParams& p, int tile_rows, int grid,
+                            int block, cudaStream_t s);
+int tiled_blocks_per_sm(bool f64, int lanes, bool map, int block, int tile_rows);
 
 // ---- analysis kernels (analysis.cu)
 cudaError_t launch_validate(int n, int nnz, const int* ptr, const int* idx, const void* vals,
@@ -70,6 +78,8 @@ cudaError_t launch_row_of_entries(int n, const int* ptr, int* rowof, cudaStream_
 // out[e] = src[index[e]] for index in [0, src_len); others reported.
 cudaError_t launch_gather(const int* src, int src_len, const int* index, int m, int* out,
                           unsigned long long* status, cudaStream_t s);
+// ipos[perm[k]] = k (perm is a permutation of 0..n-1; checked before).
+cudaError_t launch_inverse_perm(const int* perm, int n, int* ipos, cudaStream_t s);
 // Self-check of level sets: every position of jlev holds a row of the
 // level whose segment contains it, rows strictly increase inside a segment,
 // ilev[0] = 0 and ilev[nlev] = n.  Failures are reported as internal.

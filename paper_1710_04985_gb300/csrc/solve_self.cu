@@ -80,19 +80,25 @@ __global__ void __launch_bounds__(1024) self_solve_k1(SolveParams p) {
         const long long k = (long long)t * R + grp;
         const bool has_row = k < p.n;
         int i = 0, beg = 0, end = 0;
-        T bi = T(0), dinv = T(1);
+        T dinv = T(1), sum = T(0);
         if (has_row) {
             i = p.jlev[k];
             beg = p.ptr[i];
             end = p.ptr[i + 1];
             if (sl == 0) {
-                bi = b[(long long)i * p.ldb];
-                if (!p.unit) {  // 1/d(i) while the dependencies are pending, as SLFR does
+                // Everything that does not depend on x happens now, while the
+                // dependencies are pending (SLFR computes 1/d(i) up front too):
+                // the row is scaled by 1/d(i), so x(i) = b(i)/d(i) - sum of
+                // (a_ij/d(i)) x(j) and only the FMA fold and the lane reduction
+                // remain once the last dependency arrives.
+                if (!p.unit) {
                     const int q = p.diag_first ? beg : end - 1;
                     dinv = T(1) / vals[MAP ? p.vmap[q] : q];
                 }
+                sum = b[(long long)i * p.ldb] * dinv;
             }
         }
+        if (W > 1 && !p.unit) dinv = __shfl_sync(FULL, dinv, grp * W);
         // ---- per-lane chunk state: entries q0 + e*W, e < E
         int q0 = beg + sl;
         int c[E];
@@ -118,6 +124,11 @@ __global__ void __launch_bounds__(1024) self_solve_k1(SolveParams p) {
 #pragma unroll
             for (int e = 0; e < E; ++e)
                 if (live & (1u << e)) v[e] = ld_relaxed(x + (long long)c[e] * p.ldx);
+            if (!p.unit) {
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    if (live & (1u << e)) a[e] *= dinv;
+            }
 #pragma unroll
             for (int e = 0; e < E; ++e)
                 if ((live & (1u << e)) && Marker<T>::pending(v[e])) pend |= 1u << e;
@@ -125,51 +136,58 @@ __global__ void __launch_bounds__(1024) self_solve_k1(SolveParams p) {
         bool lane_done = q0 >= end;
         if (!lane_done) load_chunk();
         bool published = !has_row;
-        T sum = T(0);
         long long waits = 0;
         unsigned ns = 32;
         while (true) {
             if (!lane_done && pend == 0) {  // fold a complete chunk in entry order
 #pragma unroll
                 for (int e = 0; e < E; ++e)
-                    if (live & (1u << e)) sum += a[e] * v[e];
+                    if (live & (1u << e)) sum = fma(-a[e], v[e], sum);
                 q0 += W * E;
                 if (q0 >= end) lane_done = true;
                 else load_chunk();
             }
             const unsigned done = __ballot_sync(FULL, lane_done);
-            const bool row_ready = (done & gmask) == gmask;
-            T tot = group_sum<W>(sum, FULL);
-            if (row_ready && !published) {
-                if (sl == 0) {
-                    const T xi = (bi - tot) * dinv;
-                    if (i != p.withhold) st_relaxed(x + (long long)i * p.ldx, publishable(xi));
-                }
-                published = true;
+            const bool fresh = !published && (done & gmask) == gmask;
+            if (__any_sync(FULL, fresh)) {  // FP64 is scarce on GB300: reduce only then
+                const T tot = group_sum<W>(sum, FULL);
+                if (fresh && sl == 0 && i != p.withhold)
+                    st_relaxed(x + (long long)i * p.ldx, publishable(tot));
             }
+            published = published || fresh;
             if (__all_sync(FULL, published)) break;
-            // The wait bookkeeping below is warp-uniform (driven by __any_sync).
+            // A lane with a complete chunk folds it first (next round); only
+            // when every lane is done or waiting does the warp enter the tight
+            // wait, so a row of this ticket that another row waits on is
+            // never held back by the wait.
+            if (__any_sync(FULL, !lane_done && pend == 0)) continue;
+            // Tight wait: re-poll the pending entries until something arrives
+            // anywhere in the warp (one vote per poll; uniform control flow).
             if (__any_sync(FULL, pend != 0)) {
-                if (pend) {
+                const unsigned before = pend;
+                do {
 #pragma unroll
                     for (int e = 0; e < E; ++e)
                         if (pend & (1u << e)) v[e] = ld_relaxed(x + (long long)c[e] * p.ldx);
 #pragma unroll
                     for (int e = 0; e < E; ++e)
                         if ((pend & (1u << e)) && !Marker<T>::pending(v[e])) pend &= ~(1u << e);
-                }
-                if (++waits >= p.spin.limit) {
-                    if (pend) {
-                        report(p.status, i, kCodeTimeout);
+                    if (++waits >= p.spin.limit) {
+                        if (pend) {
+                            report(p.status, i, kCodeTimeout);
 #pragma unroll
-                        for (int e = 0; e < E; ++e)
-                            if (pend & (1u << e)) v[e] = Marker<T>::canonical_nan();
-                        pend = 0;
+                            for (int e = 0; e < E; ++e)
+                                if (pend & (1u << e)) v[e] = Marker<T>::canonical_nan();
+                            pend = 0;
+                        }
+                        waits = 0;
+                        break;
                     }
-                } else if (waits >= p.spin.hot) {
-                    __nanosleep(ns);
-                    ns = ns < p.spin.max_ns ? ns * 2 : p.spin.max_ns;
-                }
+                    if (waits >= p.spin.hot) {
+                        __nanosleep(ns);
+                        ns = ns < p.spin.max_ns ? ns * 2 : p.spin.max_ns;
+                    }
+                } while (!__any_sync(FULL, pend != before));
             } else {
                 waits = 0;
                 ns = 32;

@@ -14,7 +14,7 @@ import torch
 from . import _lib
 from ._lib import SptrsvError, check
 
-ALGOS = {"level": _lib.ALGO_LEVEL, "self": _lib.ALGO_SELF}
+ALGOS = {"level": _lib.ALGO_LEVEL, "self": _lib.ALGO_SELF, "tiled": _lib.ALGO_SELF_TILED}
 
 
 def _ptr(t):
@@ -123,7 +123,11 @@ class TriangularPlan:
         return self._keep[2]
 
     # ------------------------------------------------------------ solves
+    best_algo = "self"   # set by autotune.tune_algos; used when algo="auto"
+
     def _solve(self, fn, name, b, out, algo, stream):
+        if algo == "auto":
+            algo = self.best_algo
         if b.dtype != self.dtype or b.device != self.device:
             raise ValueError(f"{name}: b must be {self.dtype} on {self.device}")
         if out is None:
@@ -205,6 +209,21 @@ class TriangularPlan:
         check(_lib.load().sptrsv_get_tuning(self._h, ctypes.byref(a), ctypes.byref(b),
                                             ctypes.byref(c)), "sptrsv_get_tuning")
         return {"lanes_per_row": a.value, "block_size": b.value, "max_blocks": c.value}
+
+    def set_tiling(self, tile_rows, level_order=False):
+        """Tiles of the tiled self-scheduled solve (algo="tiled"): runs of
+        `tile_rows` consecutive positions of the substitution order, or of the
+        level order when `level_order`."""
+        check(_lib.load().sptrsv_set_tiling(self._h, int(tile_rows), int(bool(level_order))),
+              "sptrsv_set_tiling")
+        self._tiling = (int(tile_rows), bool(level_order))
+
+    def set_tile_rows(self, tile_rows):
+        self.set_tiling(tile_rows, self.tiling[1])
+
+    @property
+    def tiling(self):
+        return getattr(self, "_tiling", (2048, False))
 
     def set_spin_limit(self, polls):
         check(_lib.load().sptrsv_set_spin_limit(self._h, int(polls)), "sptrsv_set_spin_limit")

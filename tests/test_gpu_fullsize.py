@@ -24,10 +24,11 @@ def w2(cuda_device):
 
 
 def bench_plan(A, b, dtype=torch.float64):
-    """The plan as the benchmark builds it: analysed, then autotuned."""
+    """The plan as the benchmark builds it: analysed, then autotuned over the
+    level-ordered and tiled self-scheduled forms."""
     from paper_1710_04985_gb300 import autotune
     p = plan_for(A, dtype)
-    autotune.tune(p, torch.tensor(b, device=dev(), dtype=dtype))
+    autotune.tune_algos(p, torch.tensor(b, device=dev(), dtype=dtype))
     return p
 
 
@@ -40,7 +41,7 @@ def test_workload1_ilu_factors_forward_and_backward(w1):
             assert_levels_equal(p.levels(), A)
             assert p.levels()["nlev"] == 382
             bt = torch.tensor(b, device=dev())
-            for algo in ("self", "level"):
+            for algo in ("auto", "self", "tiled", "level"):
                 assert relerr(p.solve(bt, algo=algo), ref) <= TOL64
             assert relerr(ref, xt) <= 1e-10           # manufactured solution recovered
             assert p.status() == (0, -1)
@@ -51,7 +52,7 @@ def test_workload1_solve_pair(w1):
     L, U, xt, _, _ = w1
     b = synth.times_vector(L, synth.times_vector(U, xt))
     with bench_plan(L, b) as pl, bench_plan(U, b) as pu:
-        y = pu.solve(pl.solve(torch.tensor(b, device=dev())))
+        y = pu.solve(pl.solve(torch.tensor(b, device=dev()), algo="auto"), algo="auto")
         assert relerr(y, xt) <= 1e-10
         ref = oracle.solve(U.rowptr, U.colidx, U.vals,
                            oracle.solve(L.rowptr, L.colidx, L.vals, b, unit=True), upper=True)
@@ -83,10 +84,10 @@ def test_workload2_general_fp64_fp32(w2):
     with bench_plan(A, b) as p:
         assert_levels_equal(p.levels(), A)
         bt = torch.tensor(b, device=dev())
-        for algo in ("self", "level"):
+        for algo in ("auto", "self", "tiled", "level"):
             assert relerr(p.solve(bt, algo=algo), ref) <= TOL64
     with bench_plan(A, b, torch.float32) as p32:
-        x32 = p32.solve(torch.tensor(b, device=dev(), dtype=torch.float32))
+        x32 = p32.solve(torch.tensor(b, device=dev(), dtype=torch.float32), algo="auto")
         assert relerr(x32.double(), ref) <= TOL32
     with plan_for(A) as p:
         x, iters, rel = p.solve_refined(torch.tensor(b, device=dev()))

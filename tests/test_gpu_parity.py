@@ -76,19 +76,22 @@ def test_transpose_levels_and_pattern(name):
 
 # ---------------------------------------------------------------- solves
 
-@pytest.mark.parametrize("algo", ["self", "level"])
+@pytest.mark.parametrize("algo", ["self", "level", "tiled", "tiled_levels"])
 @pytest.mark.parametrize("name", list(MATRICES))
 def test_solve_fp64(name, algo):
     A = mat(name)
     b = synth.uniform(A.n, 11)
     ref = oracle.solve(A.rowptr, A.colidx, A.vals, b, upper=A.upper, unit=A.unit)
     with plan_for(A) as p:
+        if algo == "tiled_levels":
+            p.set_tiling(512, True)
+            algo = "tiled"
         x = p.solve(torch.tensor(b, device=dev()), algo=algo)
         assert relerr(x, ref) <= TOL64
         assert p.status() == (0, -1)
 
 
-@pytest.mark.parametrize("algo", ["self", "level"])
+@pytest.mark.parametrize("algo", ["self", "level", "tiled"])
 @pytest.mark.parametrize("name", ["general", "ilu_L", "ilu_U", "long_rows"])
 def test_solve_fp32(name, algo):
     A = mat(name)
@@ -112,10 +115,14 @@ def test_every_launch_shape(lanes, block):
             assert relerr(p.solve(bt, algo=algo), ref) <= TOL64
         p.set_tuning(lanes, block, 3)          # a tiny persistent grid still finishes
         assert relerr(p.solve(bt), ref) <= TOL64
+        for order in (False, True):            # tiled form: ragged and largest tiles
+            for tile in (32, 100, 2048, 6112):
+                p.set_tiling(tile, order)
+                assert relerr(p.solve(bt, algo="tiled"), ref) <= TOL64
 
 
 @pytest.mark.parametrize("k", [2, 3, 8, 32, 33])
-@pytest.mark.parametrize("algo", ["self", "level"])
+@pytest.mark.parametrize("algo", ["self", "level", "tiled"])
 def test_multi_rhs(k, algo):
     for name in ("general", "ilu_U"):
         A = mat(name)
@@ -126,7 +133,7 @@ def test_multi_rhs(k, algo):
             assert relerr(x, ref) <= TOL64
 
 
-@pytest.mark.parametrize("algo", ["self", "level"])
+@pytest.mark.parametrize("algo", ["self", "level", "tiled"])
 def test_leading_dimension_and_in_place(algo):
     A = mat("general")
     k, ld = 3, 5
@@ -147,15 +154,19 @@ def test_leading_dimension_and_in_place(algo):
         assert relerr(v, ref[:, 0]) <= TOL64
 
 
-@pytest.mark.parametrize("algo", ["self", "level"])
+@pytest.mark.parametrize("algo", ["self", "level", "tiled", "tiled_levels"])
 @pytest.mark.parametrize("name", ["workload0", "ilu_L", "ilu_U", "general", "general_upper",
                                   "long_rows", "unit_nodiag", "bidiag"])
 def test_solve_transpose(name, algo):
     A = mat(name)
+    level_tiles = algo == "tiled_levels"
+    algo = "tiled" if level_tiles else algo
     for k in (1, 4):
         g = synth.uniform((A.n, k) if k > 1 else A.n, 16)
         ref = oracle.solve_transpose(A.rowptr, A.colidx, A.vals, g, upper=A.upper, unit=A.unit)
         with plan_for(A) as p:
+            if level_tiles:
+                p.set_tiling(1000, True)
             y = p.solve_transpose(torch.tensor(g, device=dev()), algo=algo)
             assert relerr(y, ref) <= TOL64
 
@@ -175,6 +186,11 @@ def test_bitwise_determinism_and_algo_agreement():
         for _ in range(5):
             assert torch.equal(p.solve(bt, algo="level"), lv)
         assert relerr(lv, first.cpu().numpy()) <= 1e-14
+        # the tiled form reduces each row in the same order as the level-ordered one
+        for order in (False, True):
+            p.set_tiling(1024, order)
+            for _ in range(3):
+                assert torch.equal(p.solve(bt, algo="tiled"), first)
 
 
 # ---------------------------------------------------------------- edge cases
@@ -251,7 +267,8 @@ def test_bad_rowptr():
     assert ei.value.status == 2
 
 
-def test_timeout_is_reported_and_solve_finishes():
+@pytest.mark.parametrize("algo", ["self", "tiled"])
+def test_timeout_is_reported_and_solve_finishes(algo):
     """A row that is never published: every row that depends on it gives up
     after the spin limit, records SPTRSV_ERR_TIMEOUT and publishes NaN; rows
     independent of it are still exact.  The GPU stays usable."""
@@ -261,14 +278,14 @@ def test_timeout_is_reported_and_solve_finishes():
         p.set_spin_limit(1 << 14)
         p.withhold_row(withheld)
         b = synth.uniform(A.n, 19)
-        x = p.solve(torch.tensor(b, device=dev())).cpu().numpy()
+        x = p.solve(torch.tensor(b, device=dev()), algo=algo).cpu().numpy()
         st, row = p.status()
         assert st == 6 and row == withheld + 1
         ref = oracle.solve(A.rowptr, A.colidx, A.vals, b)
         assert relerr(x[:withheld], ref[:withheld]) <= TOL64
         assert np.all(np.isnan(x[withheld + 1:]))
         p.withhold_row(-1)
-        assert relerr(p.solve(torch.tensor(b, device=dev())), ref) <= TOL64
+        assert relerr(p.solve(torch.tensor(b, device=dev()), algo=algo), ref) <= TOL64
         assert p.status() == (0, -1)
 
 
@@ -400,3 +417,16 @@ def test_autotuner_keeps_results_exact():
         assert p.tuning["lanes_per_row"] == res["best"][0]
         assert p.tuning["max_blocks"] == res["best"][2]
         assert relerr(p.solve(bt), ref) <= TOL64
+
+
+def test_autotuner_picks_an_algorithm_and_stays_exact():
+    from paper_1710_04985_gb300 import autotune
+    A = mat("general")
+    b = synth.uniform(A.n, 33)
+    ref = oracle.solve(A.rowptr, A.colidx, A.vals, b)
+    with plan_for(A) as p:
+        bt = torch.tensor(b, device=dev())
+        res = autotune.tune_algos(p, bt, use_cache=False, lanes=(2, 8), blocks=(256,),
+                                  grids=(0, 2), tiles=(512, 2048))
+        assert res["algo"] in ("self", "tiled") and p.best_algo == res["algo"]
+        assert relerr(p.solve(bt, algo="auto"), ref) <= TOL64
