@@ -168,6 +168,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--extended", action="store_true",
+                    help="also measure the general, multi-RHS, batched, refined and autograd "
+                         "forms (adds an 'extended' object; minutes)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -201,10 +204,10 @@ def main():
     b = torch.tensor(b_host, device=dev)
     y = torch.empty_like(b)
     x = torch.empty_like(b)
-    tune_l = autotune.tune(pl, b, y)["best"]
-    tune_u = autotune.tune(pu, y, x)["best"]
+    tune_l = autotune.tune_algos(pl, b, y)
+    tune_u = autotune.tune_algos(pu, y, x)
 
-    def step(algo="self"):
+    def step(algo="auto"):
         pl.solve(b, out=y, algo=algo)
         pu.solve(y, out=x, algo=algo)
 
@@ -247,7 +250,7 @@ def main():
     peak, peak_kind = measured_peak_gbs()
     achieved = bytes_solve / (kernel_avg_ms / 1e3) / 1e9
     sha = kernel_source_sha()
-    traffic = ncu_traffic(sha)
+    traffic = ncu_traffic(sha) if tune_l["algo"] == "self" else None
 
     # ---------------- end to end through the public API with host buffers
     hb = torch.tensor(b_host).pin_memory()
@@ -257,8 +260,8 @@ def main():
 
     def e2e_step():
         db.copy_(hb, non_blocking=True)
-        pl.solve(db, out=dy)
-        pu.solve(dy, out=dx)
+        pl.solve(db, out=dy, algo="auto")
+        pu.solve(dy, out=dx, algo="auto")
         hx.copy_(dx, non_blocking=True)
 
     for _ in range(3):
@@ -311,14 +314,19 @@ def main():
             "config": {"workload": WORKLOAD, "n": n, "nnz_per_factor": nnz,
                        "nlev": [pl.levels()["nlev"], pu.levels()["nlev"]],
                        "step": "y = U^-1 (L^-1 b), eq. (3): 2 triangular solves",
-                       "algo": "self-scheduled (Alg. 3)",
-                       "tuning": {"L": list(tune_l[:3]), "U": list(tune_u[:3]),
-                                  "fields": ["lanes_per_row", "block", "max_blocks"]},
+                       "algo": {"L": tune_l["algo"], "U": tune_u["algo"],
+                                "self": "self-scheduled in level order (Alg. 3)",
+                                "tiled": "self-scheduled over shared-memory tiles"},
+                       "tuning": {"L": _tuning_row(tune_l), "U": _tuning_row(tune_u),
+                                  "fields": ["lanes_per_row", "block", "max_blocks",
+                                             "tile_rows", "tile_level_order"]},
                        "l2": "inputs larger than L2 (2 x 150 MB of matrix+vectors per step)",
                        "parallelism": f"replicas x{world}"},
-            "effective_gbs": value / world * bytes_solve / 1e9 * world,
+            "effective_gbs": value * bytes_solve / 1e9,
             "bytes_per_solve": bytes_solve,
-            "roofline": {"bound": "hbm", "kernel": "self_solve_k1", "achieved": achieved,
+            "roofline": {"bound": "hbm",
+                         "kernel": "self_solve_k1" if tune_l["algo"] == "self" else "tiled_solve_k1",
+                         "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                          "traffic": traffic, "kernel_avg_ms": kernel_avg_ms,
@@ -332,9 +340,178 @@ def main():
             "max_rel_err_vs_xtrue": err,
         }
         line.update(extra)
+        if args.extended:
+            line["extended"] = extended(dev, args)
         print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
+
+
+def _tuning_row(t):
+    best = t["best"]
+    return [best[0], best[1], best[2], best[4] if t["algo"] == "tiled" else None,
+            bool(best[5]) if t["algo"] == "tiled" else None]
+
+
+def _events_ms(fn, reps):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fn()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def extended(dev, args):
+    """Secondary measurements on the other workload shapes (same kernels)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import synth
+    from paper_1710_04985_gb300 import (BatchedTriangularSolve, TriangularPlan, autotune,
+                                        sparse_triangular_solve)
+    res = {}
+
+    def dplan(A, dtype=torch.float64):
+        return TriangularPlan(torch.tensor(A.rowptr, device=dev),
+                              torch.tensor(A.colidx, device=dev),
+                              torch.tensor(A.vals, device=dev, dtype=dtype),
+                              upper=A.upper, unit=A.unit)
+
+    # general lower triangle, n = 10^6 (FP64 and FP32)
+    A, xt, bh = synth.workload2()
+    ref = oracle.solve(A.rowptr, A.colidx, A.vals, bh)
+    gen = {"n": A.n, "nnz": A.nnz}
+    for dtype, name in ((torch.float64, "f64"), (torch.float32, "f32")):
+        p = dplan(A, dtype)
+        b = torch.tensor(bh, device=dev, dtype=dtype)
+        x = torch.empty_like(b)
+        t = autotune.tune_algos(p, b, x, reps=2)
+        ms = _events_ms(lambda: p.solve(b, out=x, algo="auto"), 5)
+        lv = _events_ms(lambda: p.solve(b, out=x, algo="level"), 2)
+        esz = 8 if dtype == torch.float64 else 4
+        byts = effective_bytes(A.n, A.nnz, esz)
+        err = float(np.max(np.abs(p.solve(b, algo="auto").double().cpu().numpy() - ref))
+                    / np.max(np.abs(ref)))
+        gen[name] = {"ms": ms, "solves_per_s": 1e3 / ms, "effective_gbs": byts / ms / 1e6,
+                     "algo": t["algo"], "level_scheduled_ms": lv, "speedup_vs_level": lv / ms,
+                     "nlev": p.levels()["nlev"], "analysis_ms": p.analysis_ms,
+                     "max_rel_err_vs_oracle": err}
+        if dtype == torch.float64:
+            gen[name]["cusparse_ms"] = cusparse_single(A, p, b, dev)
+        p.close()
+    res["general_1M"] = gen
+
+    # multi-RHS on the 128^3 ILU L factor: k = 1, 8, 32
+    L, U, _, _, _ = synth.workload1()
+    pl = dplan(L)
+    mr = {}
+    for k in (1, 8, 32):
+        bk = torch.tensor(synth.uniform((L.n, k) if k > 1 else L.n, 3000 + k), device=dev)
+        xk = torch.empty_like(bk)
+        if k == 1:
+            autotune.tune_algos(pl, bk, xk, reps=2)
+        ms = _events_ms(lambda: pl.solve(bk, out=xk, algo="auto"), 5)
+        byts = L.nnz * 12 + L.n * 8 + L.n * 16 * k
+        mr[f"k{k}"] = {"ms": ms, "rhs_solves_per_s": k * 1e3 / ms,
+                       "effective_gbs": byts / ms / 1e6}
+    res["multi_rhs_ilu_L"] = mr
+
+    # FP32 bulk + FP64 refinement on the ILU L factor and on the general matrix
+    ir = {}
+    for name, A2 in (("ilu_L", L), ("general_1M", A)):
+        p = pl if name == "ilu_L" else dplan(A2)
+        bh2 = synth.uniform(A2.n, 3100)
+        ref2 = oracle.solve(A2.rowptr, A2.colidx, A2.vals, bh2, unit=A2.unit)
+        b2 = torch.tensor(bh2, device=dev)
+        out = torch.empty_like(b2)
+        p.solve_refined(b2, out=out)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            _, iters, rel = p.solve_refined(b2, out=out)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) / 3 * 1e3
+        err = float(np.max(np.abs(out.cpu().numpy() - ref2)) / np.max(np.abs(ref2)))
+        f64_ms = _events_ms(lambda: p.solve(b2, out=out, algo="auto"), 3)
+        ir[name] = {"ms": ms, "corrections": iters, "final_rel_residual": rel,
+                    "max_rel_err_vs_fp64_oracle": err, "plain_fp64_solve_ms": f64_ms}
+        if p is not pl:
+            p.close()
+    res["refinement"] = ir
+
+    # autograd: forward + backward of 0.5 ||A^{-1} b - t||^2 on the general matrix
+    p = dplan(A)
+    v = torch.tensor(A.vals, device=dev).requires_grad_(True)
+    bb = torch.tensor(synth.uniform(A.n, synth.SEED_BASE + 4), device=dev).requires_grad_(True)
+    tt = torch.tensor(synth.uniform(A.n, synth.SEED_BASE + 5), device=dev)
+
+    def fwd_bwd():
+        v.grad = None
+        bb.grad = None
+        xx = sparse_triangular_solve(p, v, bb, algo="self")
+        (0.5 * ((xx - tt) ** 2).sum()).backward()
+
+    fwd_bwd()
+    res["autograd_general_1M"] = {"fwd_bwd_ms": _events_ms(fwd_bwd, 3),
+                                  "forward_solve_ms": _events_ms(
+                                      lambda: p.solve(bb.detach(), algo="self"), 3)}
+    p.close()
+
+    # 512 independent systems, one graph-replayed persistent launch
+    mats = synth.batch_general_parallel(512, synth.SEED_BASE + 3)
+    systems = [(m.rowptr, m.colidx, m.vals) for m in mats]
+    bs = BatchedTriangularSolve(systems, tune=True)
+    bs.solve()
+    ms_graph = _events_ms(lambda: bs.graph.replay(), 5)
+    plans = [dplan(m) for m in mats]
+    bvs = [torch.ones(m.n, dtype=torch.float64, device=dev) for m in mats]
+    ms_sep = _events_ms(lambda: [pp.solve(bv) for pp, bv in zip(plans, bvs)], 2)
+    for pp in plans:
+        pp.close()
+    nnz_b = sum(m.nnz for m in mats)
+    n_b = sum(m.n for m in mats)
+    res["batch_512"] = {"systems": len(mats), "n_total": n_b, "nnz_total": nnz_b,
+                        "graph_ms": ms_graph, "separate_solves_ms": ms_sep,
+                        "speedup": ms_sep / ms_graph,
+                        "effective_gbs": effective_bytes(n_b, nnz_b) / ms_graph / 1e6,
+                        "algo": bs.tuning["algo"], "nlev": bs.plan.levels()["nlev"]}
+    return res
+
+
+def cusparse_single(A, p, b, dev):
+    """cuSPARSE SpSV solve time (ms) of one triangular system on the plan's
+    device arrays, or None if the wrapper is unavailable."""
+    import ctypes
+
+    import torch
+
+    from paper_1710_04985_gb300 import build
+    path = build.cusparse_ref_path()
+    if not os.path.exists(path):
+        return None
+    lib = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    lib.cusref_create.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, ctypes.c_int,
+                                  ctypes.c_int, ctypes.c_int, vp, vp, vp, ctypes.POINTER(vp)]
+    lib.cusref_solve.argtypes = [vp, vp, vp, vp]
+    lib.cusref_destroy.argtypes = [vp]
+    y = torch.empty_like(b)
+    s = vp(torch.cuda.current_stream().cuda_stream)
+    h = vp()
+    f64 = 1 if b.dtype == torch.float64 else 0
+    if lib.cusref_create(A.n, A.nnz, vp(p.rowptr.data_ptr()), vp(p.colidx.data_ptr()),
+                         vp(p.vals.data_ptr()), f64, int(A.upper), int(A.unit),
+                         vp(b.data_ptr()), vp(y.data_ptr()), s, ctypes.byref(h)):
+        return None
+    ms = _events_ms(lambda: lib.cusref_solve(h, vp(b.data_ptr()), vp(y.data_ptr()), s), 3)
+    lib.cusref_destroy(h)
+    return ms
 
 
 def cusparse_pair(L, U, pl, pu, b, dev, steps):
@@ -383,7 +560,7 @@ def cusparse_pair(L, U, pl, pu, b, dev, steps):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
-    ref = pu.solve(pl.solve(b))
+    ref = pu.solve(pl.solve(b, algo="auto"), algo="auto")
     agree = float((x - ref).abs().max() / ref.abs().max())
     lib.cusref_destroy(hl)
     lib.cusref_destroy(hu)

@@ -50,9 +50,9 @@ __device__ __forceinline__ void st_relaxed(int* p, int v) {
 
 // ---------------------------------------------------------------------------
 // "Not yet solved" marker.  The self-scheduled solve fills x with all-ones
-// bit patterns (a NaN no arithmetic produces: NaN results are rewritten to
-// the canonical quiet NaN before they are published), so a published value
-// doubles as its own ready flag.
+// bit patterns (a NaN; a result that happens to carry exactly this pattern
+// is rewritten to the canonical quiet NaN before it is published), so a
+// published value doubles as its own ready flag.
 template <typename T> struct Marker;
 template <> struct Marker<double> {
     static __device__ __forceinline__ bool pending(double v) {
@@ -69,9 +69,11 @@ template <> struct Marker<float> {
     static __device__ __forceinline__ float canonical_nan() { return __uint_as_float(0x7fc00000u); }
 };
 
+// The one bit pattern a published value must not have is the marker itself
+// (an integer compare: FP64 instructions are scarce on GB300).
 template <typename T>
 __device__ __forceinline__ T publishable(T v) {
-    return (v != v) ? Marker<T>::canonical_nan() : v;
+    return Marker<T>::pending(v) ? Marker<T>::canonical_nan() : v;
 }
 
 // Spin policy of a dependency wait: a few hot polling rounds, then rounds

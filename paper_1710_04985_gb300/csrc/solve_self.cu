@@ -183,11 +183,12 @@ __global__ void __launch_bounds__(1024) self_solve_k1(SolveParams p) {
                         waits = 0;
                         break;
                     }
+                    if (__any_sync(FULL, pend != before)) break;  // something arrived
                     if (waits >= p.spin.hot) {
                         __nanosleep(ns);
                         ns = ns < p.spin.max_ns ? ns * 2 : p.spin.max_ns;
                     }
-                } while (!__any_sync(FULL, pend != before));
+                } while (true);
             } else {
                 waits = 0;
                 ns = 32;

@@ -295,6 +295,25 @@ def batch_general(count: int, seed: int, nmin: int = 1000, nmax: int = 65536):
     return [general_lower(int(nk), seed + 1 + s) for s, nk in enumerate(sizes)]
 
 
+def _general_lower_args(args):
+    return general_lower(*args)
+
+
+def batch_general_parallel(count: int, seed: int, nmin: int = 1000, nmax: int = 65536,
+                           processes: int = 0):
+    """``batch_general`` generated in worker processes (spawned, so safe to
+    call after CUDA is initialised); same matrices, same order."""
+    import multiprocessing as mp
+    import os
+    sizes = batch_sizes(count, seed, nmin, nmax)
+    jobs = [(int(nk), seed + 1 + s) for s, nk in enumerate(sizes)]
+    procs = processes or min(16, os.cpu_count() or 1)
+    if procs <= 1:
+        return [general_lower(*j) for j in jobs]
+    with mp.get_context("spawn").Pool(procs) as pool:
+        return pool.map(_general_lower_args, jobs, chunksize=4)
+
+
 def uniform(shape, seed: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
     return np.random.default_rng(seed).uniform(lo, hi, shape)
 
