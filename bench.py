@@ -168,6 +168,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--single-solve", choices=["L", "U", "G"], default=None,
+                    help="profiling target: build one plan (L or U factor of the 128^3 "
+                         "ILU(0) workload, or the n = 10^6 general matrix), apply "
+                         "--lanes/--max-blocks/--algo and run --repeat solves, nothing else")
+    ap.add_argument("--lanes", type=int, default=4)
+    ap.add_argument("--max-blocks", type=int, default=304)
+    ap.add_argument("--algo", default="self", choices=["self", "level", "tiled"])
+    ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--extended", action="store_true",
                     help="also measure the general, multi-RHS, batched, refined and autograd "
                          "forms (adds an 'extended' object; minutes)")
@@ -177,6 +185,8 @@ def main():
     world, rank, local = dist_setup()
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    if args.single_solve:
+        return single_solve(args)
 
     import numpy as np
     import torch
@@ -204,8 +214,8 @@ def main():
     b = torch.tensor(b_host, device=dev)
     y = torch.empty_like(b)
     x = torch.empty_like(b)
-    tune_l = autotune.tune_algos(pl, b, y)
-    tune_u = autotune.tune_algos(pu, y, x)
+    tune_l = autotune.tune_algos(pl, b, y, reps=5)
+    tune_u = autotune.tune_algos(pu, y, x, reps=5)
 
     def step(algo="auto"):
         pl.solve(b, out=y, algo=algo)
@@ -345,6 +355,33 @@ def main():
         print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
+
+
+def single_solve(args):
+    """A fixed plan and launch shape, `repeat` solves: the target of ncu
+    captures (the capture selects one of the solve launches)."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1710_04985_gb300 import TriangularPlan
+    dev = torch.device("cuda", 0)
+    if args.single_solve == "G":
+        A, xt, bh = synth.workload2()
+    else:
+        L, U, xt, bL, bU = synth.workload1()
+        A, bh = (L, bL) if args.single_solve == "L" else (U, bU)
+    p = TriangularPlan(torch.tensor(A.rowptr, device=dev), torch.tensor(A.colidx, device=dev),
+                       torch.tensor(A.vals, device=dev), upper=A.upper, unit=A.unit)
+    p.set_tuning(args.lanes, 256, args.max_blocks)
+    b = torch.tensor(bh, device=dev)
+    x = torch.empty_like(b)
+    for _ in range(args.repeat):
+        p.solve(b, out=x, algo=args.algo)
+    torch.cuda.synchronize()
+    err = float(np.max(np.abs(x.cpu().numpy() - xt)) / np.max(np.abs(xt)))
+    print(json.dumps({"single_solve": args.single_solve, "algo": args.algo, "lanes": args.lanes,
+                      "max_blocks": args.max_blocks, "max_rel_err_vs_xtrue": err}))
 
 
 def _tuning_row(t):

@@ -113,7 +113,14 @@ def tune_algos(plan, b, x=None, algos=("self", "tiled"), reps=3, use_cache=True,
     nrhs = 1 if b.dim() == 1 else b.shape[1]
     if nrhs > 1:
         algos = tuple(a for a in algos if a != "tiled") or ("self",)
-    per = {a: tune(plan, b, x, algo=a, reps=reps, use_cache=use_cache, **kw) for a in algos}
+    per = {}
+    for a in algos:
+        if a == "tiled" and not kw:
+            # a lighter search: the tiled form wins only on chain-like matrices
+            per[a] = tune(plan, b, x, algo=a, reps=reps, use_cache=use_cache, lanes=(1, 4, 16),
+                          blocks=(256, 512), grids=(0, 2), tiles=(512, 2048))
+        else:
+            per[a] = tune(plan, b, x, algo=a, reps=reps, use_cache=use_cache, **kw)
     name = min(per, key=lambda a: per[a]["best"][3])
     _apply(plan, per[name]["best"], name)
     plan.best_algo = name

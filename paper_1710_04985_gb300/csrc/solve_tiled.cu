@@ -82,7 +82,8 @@ __global__ void __launch_bounds__(1024) tiled_solve_k1(SolveParams p, int tile_r
                         const int q = p.diag_first ? beg : end - 1;
                         dinv = T(1) / vals[MAP ? p.vmap[q] : q];
                     }
-                    sum = b[(long long)i * p.ldb] * dinv;
+                    sum = b[(long long)i * p.ldb];
+                    if (!p.unit) sum *= dinv;
                 }
             }
             if (W > 1 && !p.unit) dinv = __shfl_sync(FULL, dinv, grp * W);
