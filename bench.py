@@ -125,6 +125,23 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(ms, pg, device):
+    """The slowest rank's elapsed milliseconds (every rank gets the result);
+    with no process group, the local value."""
+    if pg is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank, world, ms):
+    """Whole-job throughput: every rank processed `units_per_rank` units
+    (weak scaling), in the slowest rank's `ms`."""
+    return units_per_rank * world / (ms / 1e3)
+
+
 def time_oracle_pair(L, U, b, budget_s, max_pairs=None):
     import oracle
     pairs, t0 = 0, time.perf_counter()
@@ -249,12 +266,8 @@ def main():
     pl.profile(False)
     pu.profile(False)
     launches = args.steps * 4
-    if pg:
-        t = torch.tensor([ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
-    solves = 2 * args.steps * world
-    value = solves / (ms / 1e3)
+    ms = max_over_ranks(ms, pg, dev)
+    value = aggregate_rate(2 * args.steps, world, ms)
     bytes_solve = effective_bytes(n, nnz)
     kernel_avg_ms = (kl_ms + ku_ms) / max(1, kl_n + ku_n)
     peak, peak_kind = measured_peak_gbs()

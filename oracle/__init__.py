@@ -35,7 +35,12 @@ def _load():
     path = _build.library_path()
     if not os.path.exists(path) or _build.is_stale():
         _build.build()
-    lib = ctypes.CDLL(path)
+    _lib = _bind(ctypes.CDLL(path))
+    return _lib
+
+
+def _bind(lib):
+    """Declare the C signatures on a loaded copy of the oracle library."""
     i, p_i, p_d = ctypes.c_int, _I32P, _F64P
     lib.oracle_levels_rowwise.argtypes = [i, p_i, p_i, i, p_i]
     lib.oracle_levels_rowwise.restype = i
@@ -51,7 +56,6 @@ def _load():
     lib.oracle_grad_vals.restype = None
     lib.oracle_residual.argtypes = [i, p_i, p_i, p_d, i, i, p_d, i, p_d, i, p_d, i]
     lib.oracle_residual.restype = None
-    _lib = lib
     return lib
 
 

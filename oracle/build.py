@@ -23,12 +23,14 @@ def is_stale() -> bool:
     return (not os.path.exists(out)) or os.path.getmtime(out) < os.path.getmtime(SRC)
 
 
-def build(verbose: bool = False) -> str:
+def build(verbose: bool = False, src: str = SRC, out: str = "") -> str:
+    """Compile `src` (default: the oracle) into `out` (default: the oracle
+    library path)."""
     os.makedirs(OUT_DIR, exist_ok=True)
-    out = library_path()
+    out = out or library_path()
     tmp = out + ".tmp.%d" % os.getpid()
     cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-Wall", "-Wextra",
-           SRC, "-o", tmp]
+           src, "-o", tmp]
     if verbose:
         print(" ".join(cmd))
     subprocess.run(cmd, check=True)
