@@ -312,12 +312,20 @@ def main():
         a1.record()
         torch.cuda.synchronize()
         lv_ms = a0.elapsed_time(a1) / lv_steps
+        # the same per-level launch sequence captured once in a CUDA graph
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            step("level")
+        lvg_ms = _events_ms(g.replay, lv_steps)
         extra["level_scheduled"] = {"solves_per_s": 2e3 / lv_ms, "ms_per_step": lv_ms,
                                     "effective_gbs": 2 * bytes_solve / (lv_ms / 1e3) / 1e9,
-                                    "launches_per_step": 2 * 382}
+                                    "launches_per_step": 2 * 382,
+                                    "graph_ms_per_step": lvg_ms,
+                                    "graph_solves_per_s": 2e3 / lvg_ms}
         extra["cusparse_spsv"] = cusparse_pair(L, U, pl, pu, b, dev, lv_steps)
         self_ms = ms / args.steps
         extra["speedup_vs_level"] = lv_ms / self_ms
+        extra["speedup_vs_level_graph"] = lvg_ms / self_ms
         if extra["cusparse_spsv"].get("ms_per_step"):
             extra["speedup_vs_cusparse"] = extra["cusparse_spsv"]["ms_per_step"] / self_ms
 

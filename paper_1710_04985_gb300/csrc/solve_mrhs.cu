@@ -68,17 +68,22 @@ __global__ void __launch_bounds__(1024) solve_mrhs_k(SolveParams p) {
             i = p.jlev[k];
             beg = p.ptr[i];
             end = p.ptr[i + 1];
-            if (!p.unit) {
+            if (!p.unit) {  // computed while the dependencies are pending
                 const int q = p.diag_first ? beg : end - 1;
                 dinv = T(1) / vals[MAP ? p.vmap[q] : q];
             }
         }
-        // per-lane state: column `col`, next entry q0, chunk of E entries
+        // per-lane state: column `col`, next entry q0, chunk of E entries; the
+        // row is scaled by 1/d(i) so the column's value is the fold itself.
         int q0 = beg;
         int c[E];
         T a[E], v[E];
         unsigned live = 0, pend = 0;
         T acc = T(0);
+        auto start_column = [&]() {
+            acc = b[(long long)i * p.ldb + col];
+            if (!p.unit) acc *= dinv;
+        };
         auto load_chunk = [&]() {
             live = pend = 0;
 #pragma unroll
@@ -99,53 +104,69 @@ __global__ void __launch_bounds__(1024) solve_mrhs_k(SolveParams p) {
 #pragma unroll
             for (int e = 0; e < E; ++e)
                 if (live & (1u << e)) v[e] = ld_relaxed(x + (long long)c[e] * p.ldx + col);
+            if (!p.unit) {
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    if (live & (1u << e)) a[e] *= dinv;
+            }
 #pragma unroll
             for (int e = 0; e < E; ++e)
                 if ((live & (1u << e)) && Marker<T>::pending(v[e])) pend |= 1u << e;
         };
-        if (!lane_done) load_chunk();
+        if (!lane_done) {
+            start_column();
+            load_chunk();
+        }
         long long waits = 0;
         unsigned ns = 32;
         while (true) {
             if (!lane_done && pend == 0) {
 #pragma unroll
                 for (int e = 0; e < E; ++e)
-                    if (live & (1u << e)) acc += a[e] * v[e];
+                    if (live & (1u << e)) acc = fma(-a[e], v[e], acc);
                 q0 += E;
                 if (q0 >= end) {  // column done: publish it, move to the next tile
-                    const T xi = (b[(long long)i * p.ldb + col] - acc) * dinv;
-                    if (i != p.withhold) st_relaxed(x + (long long)i * p.ldx + col, publishable(xi));
+                    if (i != p.withhold) st_relaxed(x + (long long)i * p.ldx + col, publishable(acc));
                     col += W;
-                    acc = T(0);
                     q0 = beg;
-                    if (col >= p.nrhs) lane_done = true;
-                    else load_chunk();
+                    if (col >= p.nrhs) {
+                        lane_done = true;
+                    } else {
+                        start_column();
+                        load_chunk();
+                    }
                 } else {
                     load_chunk();
                 }
             }
             if (__all_sync(FULL, lane_done)) break;
+            if (__any_sync(FULL, !lane_done && pend == 0)) continue;  // fold first
             if (__any_sync(FULL, pend != 0)) {
-                if (pend) {
+                const unsigned before = pend;
+                do {
 #pragma unroll
                     for (int e = 0; e < E; ++e)
                         if (pend & (1u << e)) v[e] = ld_relaxed(x + (long long)c[e] * p.ldx + col);
 #pragma unroll
                     for (int e = 0; e < E; ++e)
                         if ((pend & (1u << e)) && !Marker<T>::pending(v[e])) pend &= ~(1u << e);
-                }
-                if (++waits >= p.spin.limit) {
-                    if (pend) {
-                        report(p.status, i, kCodeTimeout);
+                    if (++waits >= p.spin.limit) {
+                        if (pend) {
+                            report(p.status, i, kCodeTimeout);
 #pragma unroll
-                        for (int e = 0; e < E; ++e)
-                            if (pend & (1u << e)) v[e] = Marker<T>::canonical_nan();
-                        pend = 0;
+                            for (int e = 0; e < E; ++e)
+                                if (pend & (1u << e)) v[e] = Marker<T>::canonical_nan();
+                            pend = 0;
+                        }
+                        waits = 0;
+                        break;
                     }
-                } else if (waits >= p.spin.hot) {
-                    __nanosleep(ns);
-                    ns = ns < p.spin.max_ns ? ns * 2 : p.spin.max_ns;
-                }
+                    if (__any_sync(FULL, pend != before)) break;
+                    if (waits >= p.spin.hot) {
+                        __nanosleep(ns);
+                        ns = ns < p.spin.max_ns ? ns * 2 : p.spin.max_ns;
+                    }
+                } while (true);
             } else {
                 waits = 0;
                 ns = 32;
