@@ -50,18 +50,26 @@ def measured_peak_gbs():
         return 6800.0, "fallback"
 
 
-def kernel_source_sha():
+# Solve kernel of each self-scheduled form: (kernel name, source file, ncu summary)
+KERNELS = {
+    "self": ("self_solve_k1", "solve_self.cu", "self_solve_k1_ilu0_7pt_128.md"),
+    "tiled": ("tiled_solve_k1", "solve_tiled.cu", "tiled_solve_k1_ilu0_7pt_128.md"),
+    "chains": ("chain_solve_k1", "solve_chain.cu", "chain_solve_k1_ilu0_7pt_128.md"),
+}
+
+
+def kernel_source_sha(algo="self"):
     h = hashlib.sha256()
-    for f in ("solve_self.cu", "common.cuh", "internal.h"):
+    for f in (KERNELS[algo][1], "common.cuh", "internal.h"):
         with open(os.path.join(ROOT, "paper_1710_04985_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
 
 
-def ncu_traffic(sha):
-    """DRAM bytes per launch of the self-scheduled kernel from the committed
+def ncu_traffic(sha, algo="self"):
+    """DRAM bytes per launch of the solve kernel of `algo` from the committed
     ncu summary, if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "self_solve_k1_ilu0_7pt_128.md")
+    path = os.path.join(ROOT, "profiles", KERNELS[algo][2])
     try:
         text = open(path).read()
     except OSError:
@@ -191,7 +199,7 @@ def main():
                          "--lanes/--max-blocks/--algo and run --repeat solves, nothing else")
     ap.add_argument("--lanes", type=int, default=4)
     ap.add_argument("--max-blocks", type=int, default=304)
-    ap.add_argument("--algo", default="self", choices=["self", "level", "tiled"])
+    ap.add_argument("--algo", default="self", choices=["self", "level", "tiled", "chains"])
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--extended", action="store_true",
                     help="also measure the general, multi-RHS, batched, refined and autograd "
@@ -272,8 +280,8 @@ def main():
     kernel_avg_ms = (kl_ms + ku_ms) / max(1, kl_n + ku_n)
     peak, peak_kind = measured_peak_gbs()
     achieved = bytes_solve / (kernel_avg_ms / 1e3) / 1e9
-    sha = kernel_source_sha()
-    traffic = ncu_traffic(sha) if tune_l["algo"] == "self" else None
+    sha = kernel_source_sha(tune_l["algo"])
+    traffic = ncu_traffic(sha, tune_l["algo"])
 
     # ---------------- end to end through the public API with host buffers
     hb = torch.tensor(b_host).pin_memory()
@@ -347,7 +355,9 @@ def main():
                        "step": "y = U^-1 (L^-1 b), eq. (3): 2 triangular solves",
                        "algo": {"L": tune_l["algo"], "U": tune_u["algo"],
                                 "self": "self-scheduled in level order (Alg. 3)",
-                                "tiled": "self-scheduled over shared-memory tiles"},
+                                "tiled": "self-scheduled over shared-memory tiles",
+                                "chains": "self-scheduled over segments of consecutive "
+                                          "rows, in-segment values passed by shuffle"},
                        "tuning": {"L": _tuning_row(tune_l), "U": _tuning_row(tune_u),
                                   "fields": ["lanes_per_row", "block", "max_blocks",
                                              "tile_rows", "tile_level_order"]},
@@ -356,7 +366,7 @@ def main():
             "effective_gbs": value * bytes_solve / 1e9,
             "bytes_per_solve": bytes_solve,
             "roofline": {"bound": "hbm",
-                         "kernel": "self_solve_k1" if tune_l["algo"] == "self" else "tiled_solve_k1",
+                         "kernel": KERNELS[tune_l["algo"]][0],
                          "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",

@@ -83,10 +83,20 @@ typedef enum {
     SPTRSV_ALGO_LEVEL = 0,        /* Alg. 1 (LEVR): one launch per level                 */
     SPTRSV_ALGO_SELF = 1,         /* Alg. 3 (SLFR): one launch, rows self-scheduled in
                                      level order                                         */
-    SPTRSV_ALGO_SELF_TILED = 2    /* Alg. 3 over tiles of consecutive rows: a block owns a
+    SPTRSV_ALGO_SELF_TILED = 2,   /* Alg. 3 over tiles of consecutive rows: a block owns a
                                      tile and serves in-tile dependencies from shared
                                      memory (Sec. 4.3 remark 2); one right-hand side,
                                      more columns fall back to SPTRSV_ALGO_SELF          */
+    SPTRSV_ALGO_SELF_CHAINS = 3   /* Alg. 3 with a warp's ticket = 32/lanes consecutive
+                                     rows of the substitution order (segments taken in
+                                     the level order of the segment graph); a
+                                     dependency inside the segment passes between lanes
+                                     without a memory round trip.  The first use per
+                                     direction and lanes runs a segment analysis
+                                     (allocates, synchronises the stream, refused with
+                                     SPTRSV_ERR_NOT_SUPPORTED during graph capture);
+                                     one right-hand side, more columns fall back to
+                                     SPTRSV_ALGO_SELF                                    */
 } sptrsv_algo_t;
 
 /* ------------------------------------------------------------------ setup */
@@ -117,10 +127,10 @@ SPTRSV_API sptrsv_status_t sptrsv_free(sptrsv_plan_t plan);
 
 /* Solves op(A) x = b with op = identity: forward substitution for a lower
  * plan, backward for an upper one (Sec. 3.1), by Alg. 1 (SPTRSV_ALGO_LEVEL)
- * or Alg. 3 (SPTRSV_ALGO_SELF).
+ * or Alg. 3 (SPTRSV_ALGO_SELF and its tiled and chained forms).
  *   d_b, d_x  device [n][ld], element type of the plan, nrhs >= 1 columns
  *   ld        leading dimension of both, ld >= nrhs
- * With SPTRSV_ALGO_SELF, x is overwritten with a "not yet solved" marker
+ * With the self-scheduled algorithms, x is overwritten with a "not yet solved" marker
  * before the solve kernel runs, so x must not alias anything else the solve
  * reads except b itself (x == b is handled with plan scratch).
  * Asynchronous; device-side failures go to sptrsv_status.  Graph capturable

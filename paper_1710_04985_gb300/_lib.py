@@ -24,7 +24,7 @@ ERR_INTERNAL = 8
 F64, F32 = 0, 1
 LOWER, UPPER = 0, 1
 NON_UNIT, UNIT = 0, 1
-ALGO_LEVEL, ALGO_SELF, ALGO_SELF_TILED = 0, 1, 2
+ALGO_LEVEL, ALGO_SELF, ALGO_SELF_TILED, ALGO_SELF_CHAINS = 0, 1, 2, 3
 
 # (name, restype, argtypes) for every entry point of include/sptrsv.h
 _c_int, _c_ll, _c_dbl = ctypes.c_int, ctypes.c_longlong, ctypes.c_double

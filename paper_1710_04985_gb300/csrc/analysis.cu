@@ -241,6 +241,132 @@ int level_sweep_blocks_per_sm(int lanes, int block) {
     return (e == cudaSuccess && nb > 0) ? nb : 1;
 }
 
+// ------------------------------------------------------------ segment sweep
+// Levels of the segment graph for the chained solve.  Segments are runs of
+// R = 32/W consecutive positions in substitution order; a segment depends on
+// the segments holding its rows' out-of-segment dependencies, and
+//     slev(S) = 1 + max slev(segments S depends on)      (0 with none).
+// Contiguous segments of a triangular matrix always form an acyclic graph
+// and every dependency points to an earlier segment, so segments are swept
+// in order by ticket, exactly as rows are in level_sweep_k; edges inside a
+// segment are ignored.  slev[] starts at -1.
+template <int W>
+__global__ void segment_sweep_k(int n, const int* __restrict__ ptr, const int* __restrict__ idx,
+                                int upper, int* slev, int* ticket, int* nslev,
+                                unsigned long long* status, SpinPolicy sp) {
+    constexpr int R = 32 / W;
+    constexpr int E = kChunk;
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int grp = lane / W;
+    const int sl = lane - grp * W;
+    const long long nseg = ((long long)n + R - 1) / R;
+    int top = 0;  // highest slev + 1 this warp published
+    int t = 0;
+    if (lane == 0) t = atomicAdd(ticket, 1);
+    t = __shfl_sync(FULL, t, 0);
+    while (t < nseg) {
+        int tn = 0;
+        if (lane == 0) tn = atomicAdd(ticket, 1);
+        const long long p0 = (long long)t * R;
+        const long long pos = p0 + grp;
+        int i = 0, beg = 0, end = 0;
+        if (pos < n) {
+            i = upper ? (int)(n - 1 - pos) : (int)pos;
+            beg = ptr[i];
+            end = ptr[i + 1];
+        }
+        int q0 = beg + sl;
+        int c[E], v[E];
+        unsigned live = 0, pend = 0;
+        auto load_chunk = [&]() {
+            live = pend = 0;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int qq = q0 + e * W;
+                c[e] = -1;
+                v[e] = -1;
+                if (qq < end) {
+                    const int cc = idx[qq];
+                    const long long cp = upper ? (long long)(n - 1 - cc) : (long long)cc;
+                    if (cc != i && cp < p0) {  // out-of-segment dependency
+                        c[e] = (int)(cp / R);
+                        live |= 1u << e;
+                    }
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                if (live & (1u << e)) v[e] = ld_relaxed(slev + c[e]);
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                if ((live & (1u << e)) && v[e] < 0) pend |= 1u << e;
+        };
+        bool lane_done = q0 >= end;
+        if (!lane_done) load_chunk();
+        int m = -1;
+        long long waits = 0;
+        unsigned ns = 32;
+        while (true) {
+            if (!lane_done && pend == 0) {
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    if (live & (1u << e)) m = max(m, v[e]);
+                q0 += W * E;
+                if (q0 >= end) lane_done = true;
+                else load_chunk();
+            }
+            if (__all_sync(FULL, lane_done)) break;
+            if (__any_sync(FULL, !lane_done && pend == 0)) continue;
+            if (pend) {
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    if (pend & (1u << e)) v[e] = ld_relaxed(slev + c[e]);
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    if ((pend & (1u << e)) && v[e] >= 0) pend &= ~(1u << e);
+            }
+            if (++waits >= sp.limit) {
+                if (pend) {
+                    report(status, i, kCodeTimeout);
+#pragma unroll
+                    for (int e = 0; e < E; ++e)
+                        if (pend & (1u << e)) v[e] = 0;
+                    pend = 0;
+                }
+                waits = 0;
+            } else if (waits >= sp.hot) {
+                __nanosleep(ns);
+                ns = ns < sp.max_ns ? ns * 2 : sp.max_ns;
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) m = max(m, __shfl_xor_sync(FULL, m, off));
+        if (lane == 0) st_relaxed(slev + t, m + 1);
+        top = max(top, m + 2);
+        t = __shfl_sync(FULL, tn, 0);
+    }
+    if (lane == 0 && top > 0) atomicMax(nslev, top);
+}
+
+cudaError_t launch_segment_sweep(int lanes, int n, const int* ptr, const int* idx, bool upper,
+                                 int* slev, int* ticket, int* nslev, unsigned long long* status,
+                                 SpinPolicy sp, int grid, int block, cudaStream_t s) {
+#define SPTRSV_SEG(WW) \
+    segment_sweep_k<WW><<<grid, block, 0, s>>>(n, ptr, idx, upper, slev, ticket, nslev, status, sp)
+    switch (lanes) {
+        case 1: SPTRSV_SEG(1); break;
+        case 2: SPTRSV_SEG(2); break;
+        case 4: SPTRSV_SEG(4); break;
+        case 8: SPTRSV_SEG(8); break;
+        case 16: SPTRSV_SEG(16); break;
+        case 32: SPTRSV_SEG(32); break;
+        default: return cudaErrorInvalidValue;
+    }
+#undef SPTRSV_SEG
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ histogram
 // count[keys[e]] += 1, with lanes holding equal keys combined first.
 __global__ void histogram_k(const int* __restrict__ keys, int m, int* count, int bins,
@@ -525,6 +651,41 @@ cudaError_t launch_verify_levels(int n, int nlev, const int* lev, const int* ile
     long long g = ((long long)n + 255) / 256;
     if (g > 4096) g = 4096;
     verify_levels_k<<<(int)g, 256, 0, s>>>(n, nlev, lev, ilev, jlev, status);
+    return cudaGetLastError();
+}
+
+// Self-check of the segment levels of the chained solve: every
+// out-of-segment dependency of a row lies in a segment of strictly lower
+// level (the chained solve's deadlock freedom rests on it).
+__global__ void verify_segments_k(int n, int R, const int* __restrict__ ptr,
+                                  const int* __restrict__ idx, int upper,
+                                  const int* __restrict__ slev, int nslev,
+                                  unsigned long long* status) {
+    for (long long ii = (long long)blockIdx.x * blockDim.x + threadIdx.x; ii < n;
+         ii += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)ii;
+        const long long pos = upper ? (long long)(n - 1 - i) : ii;
+        const long long seg = pos / R;
+        const int own = slev[seg];
+        if (own < 0 || own >= nslev) {
+            report(status, i, kCodeInternal);
+            continue;
+        }
+        for (int q = ptr[i]; q < ptr[i + 1]; ++q) {
+            const int c = idx[q];
+            const long long cp = upper ? (long long)(n - 1 - c) : (long long)c;
+            if (c != i && cp / R != seg && slev[cp / R] >= own) report(status, i, kCodeInternal);
+        }
+    }
+}
+
+cudaError_t launch_verify_segments(int n, int R, const int* ptr, const int* idx, bool upper,
+                                   const int* slev, int nslev, unsigned long long* status,
+                                   cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    long long g = ((long long)n + 255) / 256;
+    if (g > 4096) g = 4096;
+    verify_segments_k<<<(int)g, 256, 0, s>>>(n, R, ptr, idx, upper, slev, nslev, status);
     return cudaGetLastError();
 }
 

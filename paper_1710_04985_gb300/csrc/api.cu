@@ -41,6 +41,10 @@ struct Levels {
     int* jlev = nullptr;
     int* ipos = nullptr;  // inverse of jlev (level-order tiles)
     std::vector<int> h_ilev;
+    // Chained solve, per log2(lanes): segment ids in segment-level order
+    // (built on first use) and the number of segment levels.
+    int* torder[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    int nslev[6] = {0, 0, 0, 0, 0, 0};
 };
 
 struct DeviceGuard {
@@ -138,6 +142,7 @@ void free_levels(Levels& L) {
     cudaFree(L.ilev);
     cudaFree(L.jlev);
     cudaFree(L.ipos);
+    for (int* t : L.torder) cudaFree(t);
     L = Levels();
 }
 
@@ -292,6 +297,82 @@ sptrsv_status_t build_transpose(sptrsv_plan_t P, cudaStream_t s) {
     return SPTRSV_OK;
 }
 
+int log2_lanes(int lanes) {
+    int k = 0;
+    while ((1 << k) < lanes) ++k;
+    return k;
+}
+
+// Ticket order of the chained solve for one direction and sub-warp width:
+// segments of R = 32/lanes consecutive positions of the substitution order,
+// their levels in the segment graph (a sweep like the row levels of
+// Sec. 4.1), and the segment ids stably sorted by that level.  Built once
+// per (direction, lanes); allocates and synchronises s.
+sptrsv_status_t build_chain(sptrsv_plan_t P, bool trans, int lanes, cudaStream_t s) {
+    Levels& L = trans ? P->trn : P->fwd;
+    const int k = log2_lanes(lanes);
+    if (L.torder[k]) return SPTRSV_OK;
+    if (capturing(s)) return SPTRSV_ERR_NOT_SUPPORTED;
+    const int n = P->n;
+    const int R = 32 / lanes;
+    const int nseg = (int)(((long long)n + R - 1) / R);
+    const int* ptr = trans ? P->tptr : P->rowptr;
+    const int* idx = trans ? P->tidx : P->colidx;
+    const bool upper = trans ? !P->upper : P->upper;
+    const int hist_n = radix_hist_entries(nseg);
+    int* scratch = nullptr;
+    CK(cudaMalloc(&scratch, sizeof(int) * (5 * (size_t)nseg + 2 * (size_t)hist_n)));
+    int* slev = scratch;
+    int* k_a = slev + nseg;
+    int* v_a = k_a + nseg;
+    int* k_b = v_a + nseg;
+    int* v_b = k_b + nseg;
+    int* hist = v_b + nseg;
+    int* hist_scan = hist + hist_n;
+    int* torder = nullptr;
+    cudaError_t e = cudaMalloc(&torder, sizeof(int) * (size_t)nseg);
+    if (e != cudaSuccess) {
+        cudaFree(scratch);
+        return cuda_fail(e);
+    }
+    const int block = 256;
+    const long long want_blocks = ((long long)nseg + block / 32 - 1) / (block / 32);
+    long long grid = env_ll("SPTRSV_SWEEP_BLOCKS_PER_SM", 4) * P->num_sms;
+    if (grid > want_blocks) grid = want_blocks;
+    if (grid < 1) grid = 1;
+    int nslev = 0;
+    e = cudaMemsetAsync(slev, 0xff, sizeof(int) * (size_t)nseg, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P->counters, 0, 2 * sizeof(int), s);
+    if (e == cudaSuccess)
+        e = launch_segment_sweep(lanes, n, ptr, idx, upper, slev, P->counters, P->counters + 1,
+                                 P->status, P->spin, (int)grid, block, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&nslev, P->counters + 1, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    sptrsv_status_t rc = e == cudaSuccess ? SPTRSV_OK : cuda_fail(e);
+    int row = -1;
+    if (rc == SPTRSV_OK) rc = take_status(P, s, &row);
+    if (rc == SPTRSV_OK && (nslev < 1 || nslev > nseg)) rc = SPTRSV_ERR_INTERNAL;
+    if (rc == SPTRSV_OK) {
+        e = radix_sort_values(slev, nullptr, nseg, bits_for(nslev - 1), torder, k_a, v_a, k_b,
+                              v_b, hist, hist_scan, P->status, s);
+        if (e == cudaSuccess)
+            e = launch_verify_segments(n, R, ptr, idx, upper, slev, nslev, P->status, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_fail(e);
+        if (rc == SPTRSV_OK && take_status(P, s, &row) != SPTRSV_OK) rc = SPTRSV_ERR_INTERNAL;
+    }
+    cudaFree(scratch);
+    if (rc != SPTRSV_OK) {
+        if (row >= 0) g_last_error_row = row;
+        cudaFree(torder);
+        return rc;
+    }
+    L.torder[k] = torder;
+    L.nslev[k] = nslev;
+    return SPTRSV_OK;
+}
+
 sptrsv_status_t ensure_bytes(void** buf, size_t* have, size_t want, cudaStream_t s) {
     if (*have >= want) return SPTRSV_OK;
     if (capturing(s)) return SPTRSV_ERR_NOT_SUPPORTED;
@@ -329,6 +410,9 @@ sptrsv_status_t prof_end(sptrsv_plan_t P, cudaStream_t s) {
 sptrsv_status_t run_solve(sptrsv_plan_t P, bool trans, bool f64, const void* vals, const void* b,
                           long long ldb, void* x, long long ldx, int nrhs, sptrsv_algo_t algo,
                           cudaStream_t s) {
+    const bool mrhs = nrhs > 1;
+    const int lanes = mrhs ? mrhs_lanes(nrhs) : P->lanes;
+    if (algo == SPTRSV_ALGO_SELF_CHAINS && !mrhs) ST(build_chain(P, trans, lanes, s));
     const Levels& L = trans ? P->trn : P->fwd;
     SolveParams p;
     memset(&p, 0, sizeof(p));
@@ -350,8 +434,6 @@ sptrsv_status_t run_solve(sptrsv_plan_t P, bool trans, bool f64, const void* val
     p.spin = P->spin;
     p.withhold = P->withhold;
     p.ipos = (algo == SPTRSV_ALGO_SELF_TILED && P->tile_level_order) ? L.ipos : nullptr;
-    const bool mrhs = nrhs > 1;
-    const int lanes = mrhs ? mrhs_lanes(nrhs) : P->lanes;
     int launches = 0;
     if (algo == SPTRSV_ALGO_LEVEL) {
         ST(prof_begin(P, s));
@@ -392,6 +474,15 @@ sptrsv_status_t run_solve(sptrsv_plan_t P, bool trans, bool f64, const void* val
             ST(prof_begin(P, s));
             CK(launch_tiled_k1(f64, lanes, p, P->tile_rows, (int)grid, P->block, s));
             ST(prof_end(P, s));
+        } else if (algo == SPTRSV_ALGO_SELF_CHAINS && !mrhs) {
+            grid = (long long)chain_blocks_per_sm(f64, lanes, trans, P->block) * P->num_sms;
+            if (P->max_blocks > 0 && grid > P->max_blocks) grid = P->max_blocks;
+            if (grid > want_blocks) grid = want_blocks;
+            if (grid < 1) grid = 1;
+            ST(prof_begin(P, s));
+            CK(launch_chain_k1(f64, lanes, p, L.torder[log2_lanes(lanes)], (int)grid, P->block,
+                               s));
+            ST(prof_end(P, s));
         } else {
             ST(prof_begin(P, s));
             CK(mrhs ? launch_mrhs(f64, lanes, true, p, (int)grid, P->block, s)
@@ -407,7 +498,8 @@ sptrsv_status_t run_solve(sptrsv_plan_t P, bool trans, bool f64, const void* val
 sptrsv_status_t solve_common(sptrsv_plan_t P, bool trans, const void* b, void* x, int nrhs,
                              int ld, sptrsv_algo_t algo, void* stream) {
     if (!P || nrhs < 1 || ld < nrhs ||
-        (algo != SPTRSV_ALGO_LEVEL && algo != SPTRSV_ALGO_SELF && algo != SPTRSV_ALGO_SELF_TILED))
+        (algo != SPTRSV_ALGO_LEVEL && algo != SPTRSV_ALGO_SELF && algo != SPTRSV_ALGO_SELF_TILED &&
+         algo != SPTRSV_ALGO_SELF_CHAINS))
         return SPTRSV_ERR_INVALID_ARG;
     P->last_launches = 0;
     if (P->n == 0) return SPTRSV_OK;

@@ -50,6 +50,13 @@ int self_blocks_per_sm(bool f64, int lanes, bool mrhs, bool map, int block);
 cudaError_t launch_tiled_k1(bool f64, int lanes, const SolveParams& p, int tile_rows, int grid,
                             int block, cudaStream_t s);
 int tiled_blocks_per_sm(bool f64, int lanes, bool map, int block, int tile_rows);
+// Chained self-scheduled solve (solve_chain.cu): tickets are segments of
+// 32/lanes consecutive positions in substitution order, taken in the order
+// `torder` (segment ids sorted by segment level); in-segment dependencies
+// are forwarded between lanes by shuffle.
+cudaError_t launch_chain_k1(bool f64, int lanes, const SolveParams& p, const int* torder,
+                            int grid, int block, cudaStream_t s);
+int chain_blocks_per_sm(bool f64, int lanes, bool map, int block);
 
 // ---- analysis kernels (analysis.cu)
 cudaError_t launch_validate(int n, int nnz, const int* ptr, const int* idx, const void* vals,
@@ -59,6 +66,17 @@ cudaError_t launch_level_sweep(int lanes, int n, const int* ptr, const int* idx,
                                int* lev, int* ticket, int* nlev, unsigned long long* status,
                                SpinPolicy sp, int grid, int block, cudaStream_t s);
 int level_sweep_blocks_per_sm(int lanes, int block);
+// Levels of the graph of segments of 32/lanes consecutive positions in
+// substitution order (chained solve); slev[] must start at -1, *ticket and
+// *nslev at 0; *nslev ends as the number of segment levels.
+cudaError_t launch_segment_sweep(int lanes, int n, const int* ptr, const int* idx, bool upper,
+                                 int* slev, int* ticket, int* nslev, unsigned long long* status,
+                                 SpinPolicy sp, int grid, int block, cudaStream_t s);
+// Self-check: every out-of-segment dependency lies in a lower segment level
+// (segments of R positions); failures are reported as internal.
+cudaError_t launch_verify_segments(int n, int R, const int* ptr, const int* idx, bool upper,
+                                   const int* slev, int nslev, unsigned long long* status,
+                                   cudaStream_t s);
 // count[keys[e]] += 1 for keys in [0, bins); any other key is reported as
 // an internal error in *status and skipped.
 cudaError_t launch_histogram(const int* keys, int m, int* count, int bins,

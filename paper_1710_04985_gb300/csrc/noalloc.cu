@@ -141,9 +141,12 @@ __global__ void __launch_bounds__(1024)
         unsigned ns = 32;
         while (true) {
             if (!lane_done && pend == 0) {
+                const int hi = 32 - __clz(live);  // stop after the last live slot
 #pragma unroll
-                for (int e = 0; e < E; ++e)
+                for (int e = 0; e < E; ++e) {
+                    if (e >= hi) break;
                     if (live & (1u << e)) sum += a[e] * v[e];
+                }
                 q0 += W * E;
                 if (q0 >= end) lane_done = true;
                 else load_chunk();

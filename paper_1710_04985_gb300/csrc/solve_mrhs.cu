@@ -121,9 +121,7 @@ __global__ void __launch_bounds__(1024) solve_mrhs_k(SolveParams p) {
         unsigned ns = 32;
         while (true) {
             if (!lane_done && pend == 0) {
-#pragma unroll
-                for (int e = 0; e < E; ++e)
-                    if (live & (1u << e)) acc = fma(-a[e], v[e], acc);
+                acc = fold_chunk(acc, a, v, live);
                 q0 += E;
                 if (q0 >= end) {  // column done: publish it, move to the next tile
                     if (i != p.withhold) st_relaxed(x + (long long)i * p.ldx + col, publishable(acc));

@@ -138,9 +138,7 @@ __global__ void __launch_bounds__(1024) tiled_solve_k1(SolveParams p, int tile_r
             unsigned ns = 32;
             while (true) {
                 if (!lane_done && pend == 0) {
-#pragma unroll
-                    for (int e = 0; e < E; ++e)
-                        if (live & (1u << e)) sum = fma(-a[e], v[e], sum);
+                    sum = fold_chunk(sum, a, v, live);
                     q0 += W * E;
                     if (q0 >= end) lane_done = true;
                     else load_chunk();

@@ -14,7 +14,8 @@ import torch
 from . import _lib
 from ._lib import SptrsvError, check
 
-ALGOS = {"level": _lib.ALGO_LEVEL, "self": _lib.ALGO_SELF, "tiled": _lib.ALGO_SELF_TILED}
+ALGOS = {"level": _lib.ALGO_LEVEL, "self": _lib.ALGO_SELF, "tiled": _lib.ALGO_SELF_TILED,
+         "chains": _lib.ALGO_SELF_CHAINS}
 
 
 def _ptr(t):

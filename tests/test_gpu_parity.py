@@ -76,7 +76,7 @@ def test_transpose_levels_and_pattern(name):
 
 # ---------------------------------------------------------------- solves
 
-@pytest.mark.parametrize("algo", ["self", "level", "tiled", "tiled_levels"])
+@pytest.mark.parametrize("algo", ["self", "level", "tiled", "tiled_levels", "chains"])
 @pytest.mark.parametrize("name", list(MATRICES))
 def test_solve_fp64(name, algo):
     A = mat(name)
@@ -91,7 +91,7 @@ def test_solve_fp64(name, algo):
         assert p.status() == (0, -1)
 
 
-@pytest.mark.parametrize("algo", ["self", "level", "tiled"])
+@pytest.mark.parametrize("algo", ["self", "level", "tiled", "chains"])
 @pytest.mark.parametrize("name", ["general", "ilu_L", "ilu_U", "long_rows"])
 def test_solve_fp32(name, algo):
     A = mat(name)
@@ -111,10 +111,11 @@ def test_every_launch_shape(lanes, block):
     with plan_for(A) as p:
         p.set_tuning(lanes, block, 0)
         bt = torch.tensor(b, device=dev())
-        for algo in ("self", "level"):
+        for algo in ("self", "level", "chains"):
             assert relerr(p.solve(bt, algo=algo), ref) <= TOL64
         p.set_tuning(lanes, block, 3)          # a tiny persistent grid still finishes
         assert relerr(p.solve(bt), ref) <= TOL64
+        assert relerr(p.solve(bt, algo="chains"), ref) <= TOL64
         for order in (False, True):            # tiled form: ragged and largest tiles
             for tile in (32, 100, 2048, 6112):
                 p.set_tiling(tile, order)
@@ -122,7 +123,7 @@ def test_every_launch_shape(lanes, block):
 
 
 @pytest.mark.parametrize("k", [2, 3, 8, 32, 33])
-@pytest.mark.parametrize("algo", ["self", "level", "tiled"])
+@pytest.mark.parametrize("algo", ["self", "level", "tiled", "chains"])
 def test_multi_rhs(k, algo):
     for name in ("general", "ilu_U"):
         A = mat(name)
@@ -133,7 +134,7 @@ def test_multi_rhs(k, algo):
             assert relerr(x, ref) <= TOL64
 
 
-@pytest.mark.parametrize("algo", ["self", "level", "tiled"])
+@pytest.mark.parametrize("algo", ["self", "level", "tiled", "chains"])
 def test_leading_dimension_and_in_place(algo):
     A = mat("general")
     k, ld = 3, 5
@@ -154,7 +155,7 @@ def test_leading_dimension_and_in_place(algo):
         assert relerr(v, ref[:, 0]) <= TOL64
 
 
-@pytest.mark.parametrize("algo", ["self", "level", "tiled", "tiled_levels"])
+@pytest.mark.parametrize("algo", ["self", "level", "tiled", "tiled_levels", "chains"])
 @pytest.mark.parametrize("name", ["workload0", "ilu_L", "ilu_U", "general", "general_upper",
                                   "long_rows", "unit_nodiag", "bidiag"])
 def test_solve_transpose(name, algo):
@@ -186,11 +187,14 @@ def test_bitwise_determinism_and_algo_agreement():
         for _ in range(5):
             assert torch.equal(p.solve(bt, algo="level"), lv)
         assert relerr(lv, first.cpu().numpy()) <= 1e-14
-        # the tiled form reduces each row in the same order as the level-ordered one
+        # the tiled and chained forms reduce each row in the same order as the
+        # level-ordered one
         for order in (False, True):
             p.set_tiling(1024, order)
             for _ in range(3):
                 assert torch.equal(p.solve(bt, algo="tiled"), first)
+        for _ in range(3):
+            assert torch.equal(p.solve(bt, algo="chains"), first)
 
 
 # ---------------------------------------------------------------- edge cases
@@ -267,7 +271,7 @@ def test_bad_rowptr():
     assert ei.value.status == 2
 
 
-@pytest.mark.parametrize("algo", ["self", "tiled"])
+@pytest.mark.parametrize("algo", ["self", "tiled", "chains"])
 def test_timeout_is_reported_and_solve_finishes(algo):
     """A row that is never published: every row that depends on it gives up
     after the spin limit, records SPTRSV_ERR_TIMEOUT and publishes NaN; rows
@@ -428,5 +432,5 @@ def test_autotuner_picks_an_algorithm_and_stays_exact():
         bt = torch.tensor(b, device=dev())
         res = autotune.tune_algos(p, bt, use_cache=False, lanes=(2, 8), blocks=(256,),
                                   grids=(0, 2), tiles=(512, 2048))
-        assert res["algo"] in ("self", "tiled") and p.best_algo == res["algo"]
+        assert res["algo"] in ("self", "tiled", "chains") and p.best_algo == res["algo"]
         assert relerr(p.solve(bt, algo="auto"), ref) <= TOL64
