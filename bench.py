@@ -55,6 +55,7 @@ KERNELS = {
     "self": ("self_solve_k1", "solve_self.cu", "self_solve_k1_ilu0_7pt_128.md"),
     "tiled": ("tiled_solve_k1", "solve_tiled.cu", "tiled_solve_k1_ilu0_7pt_128.md"),
     "chains": ("chain_solve_k1", "solve_chain.cu", "chain_solve_k1_ilu0_7pt_128.md"),
+    "permuted": ("self_solve_k1", "solve_self.cu", "self_solve_k1_permuted_ilu0_7pt_128.md"),
 }
 
 
@@ -204,6 +205,12 @@ def main():
     ap.add_argument("--extended", action="store_true",
                     help="also measure the general, multi-RHS, batched, refined and autograd "
                          "forms (adds an 'extended' object; minutes)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="instead of the headline line, print the Table 2 sweep: the solve "
+                         "pair of eq. (3) on the 5/9-point 2-D and 7/27-point 3-D Laplacians "
+                         "of every Table 2 grid, FP64 and FP32 (minutes)")
+    ap.add_argument("--sweep-grids", type=int, default=5,
+                    help="grids per stencil in --sweep (the first k of Table 2)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -212,6 +219,8 @@ def main():
         return run_reference(args, world, rank)
     if args.single_solve:
         return single_solve(args)
+    if args.sweep:
+        return table2_sweep(args)
 
     import numpy as np
     import torch
@@ -332,6 +341,21 @@ def main():
                                     "graph_solves_per_s": 2e3 / lvg_ms}
         extra["cusparse_spsv"] = cusparse_pair(L, U, pl, pu, b, dev, lv_steps)
         self_ms = ms / args.steps
+        # setup phase (Sec. 4.4): the sync-free sweep against Kahn's algorithm
+        # (Sec. 4.4.1), as the paper runs it (host loop) and in one persistent
+        # launch; every method yields the same levels
+        methods = {}
+        for m in ("sweep", "kahn_host_loop", "kahn_persistent"):
+            methods[m] = [pl.reanalyze(m), pu.reanalyze(m)]
+        best_setup = min(sum(v) for v in methods.values())
+        extra["analysis_methods_ms"] = {"L_U": methods, "fields": "[L, U] wall ms, level "
+                                        "analysis + level sets (+ transposed pattern for Kahn)"}
+        cus = extra["cusparse_spsv"]
+        if cus.get("ms_per_step"):
+            # Sec. 5.2: smallest number of solve pairs n_s for which setup +
+            # n_s solves beats cuSPARSE SpSV's setup + n_s solves
+            extra["break_even_solves_vs_cusparse"] = _break_even(
+                best_setup, self_ms, cus["analysis_ms_both"], cus["ms_per_step"])
         extra["speedup_vs_level"] = lv_ms / self_ms
         extra["speedup_vs_level_graph"] = lvg_ms / self_ms
         if extra["cusparse_spsv"].get("ms_per_step"):
@@ -357,7 +381,9 @@ def main():
                                 "self": "self-scheduled in level order (Alg. 3)",
                                 "tiled": "self-scheduled over shared-memory tiles",
                                 "chains": "self-scheduled over segments of consecutive "
-                                          "rows, in-segment values passed by shuffle"},
+                                          "rows, in-segment values passed by shuffle",
+                                "permuted": "self-scheduled in level order on a level-ordered "
+                                            "copy of the matrix (Sec. 4.3 remark 2)"},
                        "tuning": {"L": _tuning_row(tune_l), "U": _tuning_row(tune_u),
                                   "fields": ["lanes_per_row", "block", "max_blocks",
                                              "tile_rows", "tile_level_order"]},
@@ -413,6 +439,85 @@ def single_solve(args):
     err = float(np.max(np.abs(x.cpu().numpy() - xt)) / np.max(np.abs(xt)))
     print(json.dumps({"single_solve": args.single_solve, "algo": args.algo, "lanes": args.lanes,
                       "max_blocks": args.max_blocks, "max_rel_err_vs_xtrue": err}))
+
+
+def table2_sweep(args):
+    """Sec. 5.1: the solve pair y = (U+D)^{-1} (L+D)^{-1} b of eq. (3) on the
+    5/9-point 2-D and 7/27-point 3-D Laplacians of the Table 2 grids (aspect
+    ratios of eq. (5)), in FP64 and FP32, for the self-scheduled solve (tuned),
+    the level-scheduled solve and cuSPARSE SpSV on the same arrays.  GFLOPS
+    follows eq. (4): 2 nnz(A) / t for the pair.  b is manufactured from a
+    seeded x_true, and each row reports the error of the solution."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1710_04985_gb300 import TriangularPlan, autotune
+    dev = torch.device("cuda", 0)
+    rows = []
+    cases = [(dims, pts) for pts in (5, 9) for dims in synth.TABLE2_GRIDS_2D[:args.sweep_grids]]
+    cases += [(dims, pts) for pts in (7, 27) for dims in synth.TABLE2_GRIDS_3D[:args.sweep_grids]]
+    for dims, pts in cases:
+        L, U = synth.laplacian_triangles(dims, pts)
+        xt = synth.uniform(L.n, synth.SEED_BASE + 10 + pts)
+        bh = synth.times_vector(L, synth.times_vector(U, xt))
+        nnz_a = L.nnz + U.nnz - L.n
+        for dtype, dname in ((torch.float64, "f64"), (torch.float32, "f32")):
+            def dplan(A):
+                return TriangularPlan(torch.tensor(A.rowptr, device=dev),
+                                      torch.tensor(A.colidx, device=dev),
+                                      torch.tensor(A.vals, device=dev, dtype=dtype),
+                                      upper=A.upper, unit=A.unit)
+            pl, pu = dplan(L), dplan(U)
+            b = torch.tensor(bh, device=dev, dtype=dtype)
+            y, x = torch.empty_like(b), torch.empty_like(b)
+            kw = dict(algos=("self", "permuted"), lanes=(1, 2, 4, 8, 16), blocks=(256, 512),
+                      grids=(0, 2), reps=3)
+            tl = autotune.tune_algos(pl, b, y, **kw)
+            pl.solve(b, out=y, algo="auto")
+            tu = autotune.tune_algos(pu, y, x, **kw)
+
+            def pair(algo):
+                pl.solve(b, out=y, algo=algo)
+                pu.solve(y, out=x, algo=algo)
+
+            ms = _events_ms(lambda: pair("auto"), 10)
+            err = float(np.max(np.abs(x.double().cpu().numpy() - xt)) / np.max(np.abs(xt)))
+            lv_ms = _events_ms(lambda: pair("level"), 2)
+            esz = 8 if dtype == torch.float64 else 4
+            byts = effective_bytes(L.n, L.nnz, esz) + effective_bytes(U.n, U.nnz, esz)
+            cus = None
+            if dtype == torch.float64:
+                cl = cusparse_single(L, pl, b, dev)
+                cu = cusparse_single(U, pu, y, dev)
+                cus = cl + cu if cl is not None and cu is not None else None
+            row = {"grid": "x".join(map(str, dims)), "points": pts, "dtype": dname,
+                   "n": L.n, "nnz_A": nnz_a,
+                   "aspect": dims[1] // dims[0] if len(dims) == 2 else dims[2] // dims[0],
+                   "nlev": [pl.levels()["nlev"], pu.levels()["nlev"]],
+                   "self_ms": ms, "gflops": 2 * nnz_a / (ms / 1e3) / 1e9,
+                   "effective_gbs": byts / (ms / 1e3) / 1e9,
+                   "us_per_level": 1e3 * ms / (pl.levels()["nlev"] + pu.levels()["nlev"]),
+                   "level_ms": lv_ms, "speedup_vs_level": lv_ms / ms,
+                   "cusparse_ms": cus, "speedup_vs_cusparse": (cus / ms) if cus else None,
+                   "lanes": [tl["best"][0], tu["best"][0]], "algo": [tl["algo"], tu["algo"]],
+                   "max_rel_err_vs_xtrue": err}
+            rows.append(row)
+            print(json.dumps(row), file=sys.stderr, flush=True)
+            pl.close()
+            pu.close()
+    print(json.dumps({"sweep": "table2", "unit_note": "ms per solve pair (L then U)",
+                      "rows": rows}), flush=True)
+
+
+def _break_even(setup_a, solve_a, setup_b, solve_b):
+    """Smallest n >= 0 with setup_a + n solve_a < setup_b + n solve_b (None
+    if never)."""
+    if setup_a < setup_b:
+        return 0
+    if solve_a >= solve_b:
+        return None
+    return int((setup_a - setup_b) // (solve_b - solve_a)) + 1
 
 
 def _tuning_row(t):

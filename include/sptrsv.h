@@ -35,7 +35,10 @@
  *  The caller owns every array it passes.  The plan BORROWS d_rowptr,
  *  d_colidx and d_vals: they must stay valid, with the same pattern, until
  *  sptrsv_free.  Values may change between solves without re-analysis (the
- *  ILU refactorisation case of Sec. 1).  The plan OWNS its level arrays, the
+ *  ILU refactorisation case of Sec. 1); the plan's copies of the values (the
+ *  FP32 copy of the refined solve, the level-ordered copy of
+ *  SPTRSV_ALGO_SELF_PERMUTED) are brought up to date by
+ *  sptrsv_refresh_values.  The plan OWNS its level arrays, the
  *  transposed pattern, its counters, its status word and its scratch.
  *  Solves on one plan must be serialised (one stream at a time): they share
  *  the plan's counters and scratch.
@@ -96,8 +99,52 @@ typedef enum {
                                      (allocates, synchronises the stream, refused with
                                      SPTRSV_ERR_NOT_SUPPORTED during graph capture);
                                      one right-hand side, more columns fall back to
-                                     SPTRSV_ALGO_SELF                                    */
+                                     SPTRSV_ALGO_SELF                                    */,
+    SPTRSV_ALGO_SELF_PERMUTED = 4 /* Alg. 3 on a level-ordered copy of the matrix: row k
+                                     of the copy is row jlev[k], columns renumbered to
+                                     positions in jlev, values copied (the preordering
+                                     of Sec. 4.3 remark 2), so a warp's rows and the
+                                     unknowns it waits on are contiguous.  Same
+                                     arithmetic in the same order as SPTRSV_ALGO_SELF
+                                     (bitwise equal results for equal tuning).  The
+                                     first use per direction builds the copy
+                                     (allocates ~12 B per entry + 12 B per row in FP64,
+                                     synchronises the stream, refused with
+                                     SPTRSV_ERR_NOT_SUPPORTED during graph capture).
+                                     The copy is a SNAPSHOT of the values: after
+                                     changing d_vals in place call
+                                     sptrsv_refresh_values (sptrsv_set_values does it).
+                                     One right-hand side; more columns fall back to
+                                     SPTRSV_ALGO_SELF                                    */,
+    SPTRSV_ALGO_SELF_COLUMN = 5   /* Alg. 4 (SLFC): column-wise self-scheduled solve.
+                                     Unknowns in level order wait on a dependency
+                                     counter, then push a(r,i) x(i) into every
+                                     dependent x(r) with FP atomic adds and decrement
+                                     its counter.  The order of the adds is not fixed:
+                                     results agree with the row-wise forms to rounding
+                                     but are not bitwise reproducible.  x must not
+                                     alias b except in place (x == b).  The first use
+                                     per direction builds the counters (and the
+                                     transposed pattern, which holds the columns of a
+                                     lower/upper matrix): allocates, synchronises the
+                                     stream, refused with SPTRSV_ERR_NOT_SUPPORTED
+                                     during graph capture.  One right-hand side; more
+                                     columns fall back to SPTRSV_ALGO_SELF               */
 } sptrsv_algo_t;
+
+/* Level-analysis methods (sptrsv_reanalyze).  All give the same levels and
+ * level sets (levels are unique); they differ in cost. */
+typedef enum {
+    SPTRSV_ANALYSIS_SWEEP = 0,            /* default: one persistent sync-free sweep
+                                             in substitution order, lev(i) = 1 + max
+                                             lev(j) computed as a (max,+) solve      */
+    SPTRSV_ANALYSIS_KAHN_HOST_LOOP = 1,   /* Kahn's algorithm as in Sec. 4.4.1: one
+                                             launch and one device-to-host copy per
+                                             level                                  */
+    SPTRSV_ANALYSIS_KAHN_PERSISTENT = 2   /* Kahn's algorithm in one cooperative
+                                             launch, levels separated by a bounded
+                                             grid-wide barrier                      */
+} sptrsv_analysis_t;
 
 /* ------------------------------------------------------------------ setup */
 
@@ -119,6 +166,18 @@ SPTRSV_API sptrsv_status_t sptrsv_analyze(int n, int nnz, const int *d_rowptr,
                                sptrsv_dtype_t dtype, sptrsv_uplo_t uplo,
                                sptrsv_diag_t diag, void *stream,
                                sptrsv_plan_t *plan);
+
+/* Recomputes the levels and level sets of the forward (transpose = 0) or
+ * transposed (transpose = 1) system with `method` (Sec. 4.4: the setup
+ * phase; Sec. 4.4.1: Kahn's algorithm on the GPU), replacing the plan's.  The
+ * result is identical for every method; the wall time of this call, from
+ * after a first synchronisation of `stream` to the end, including a
+ * transposed pattern it had to build (Table 1's TRANS_GPU, which Kahn's
+ * algorithm needs for the forward system), is what sptrsv_analysis_ms then
+ * returns.  Allocates and synchronises; refused with
+ * SPTRSV_ERR_NOT_SUPPORTED during graph capture. */
+SPTRSV_API sptrsv_status_t sptrsv_reanalyze(sptrsv_plan_t plan, int transpose,
+                                            sptrsv_analysis_t method, void *stream);
 
 /* Releases everything the plan owns (synchronises the device first). */
 SPTRSV_API sptrsv_status_t sptrsv_free(sptrsv_plan_t plan);
@@ -195,12 +254,15 @@ SPTRSV_API sptrsv_status_t sptrsv_solve_refined(sptrsv_plan_t plan, const double
 
 /* Points the plan at a new values array with the same pattern and element
  * type (for example a new parameter tensor); borrowed like the first one.
- * The FP32 copy, if any, is refreshed on `stream`.  The diagonal is not
+ * The plan's copies of the values (FP32, level-ordered), if any, are
+ * refreshed on `stream`.  The diagonal is not
  * re-checked: it must stay nonzero.  Asynchronous. */
 SPTRSV_API sptrsv_status_t sptrsv_set_values(sptrsv_plan_t plan, const void *d_vals,
                                              void *stream);
 
-/* Re-reads d_vals into the plan's FP32 copy (if one exists).  Async. */
+/* Re-reads d_vals into the plan's copies of the values, if they exist: the
+ * FP32 copy of sptrsv_solve_refined and the level-ordered copies of
+ * SPTRSV_ALGO_SELF_PERMUTED.  Async. */
 SPTRSV_API sptrsv_status_t sptrsv_refresh_values(sptrsv_plan_t plan, void *stream);
 
 /* ----------------------------------------------------------------- tuning */
@@ -266,8 +328,8 @@ SPTRSV_API int sptrsv_last_error_row(void);
 SPTRSV_API const char *sptrsv_status_string(sptrsv_status_t status);
 SPTRSV_API const char *sptrsv_last_cuda_error(void);
 
-/* Wall time of the last sptrsv_analyze of this plan (ms, host clock around
- * the synchronised setup). */
+/* Wall time of the last sptrsv_analyze or sptrsv_reanalyze of this plan
+ * (ms, host clock around the synchronised setup). */
 SPTRSV_API sptrsv_status_t sptrsv_analysis_ms(sptrsv_plan_t plan, double *ms);
 
 /* Kernel timing.  While enabled, every solve records a pair of CUDA events

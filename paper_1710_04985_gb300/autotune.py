@@ -6,8 +6,9 @@ sub-warp width (lanes per row, hence rows per warp = 32 / lanes) at the
 default block size, then, for that width, the block size and the cap on the
 persistent grid (how many warps wait ahead of the dependency frontier: more
 hides latency, fewer polls less L2 traffic), and for the tiled form the tile
-size.  ``tune_algos`` runs ``tune`` for the level-ordered, tiled and chained
-self-scheduled forms and keeps the fastest, recording it on the plan.
+size.  ``tune_algos`` runs ``tune`` for the level-ordered (in place and on
+the level-ordered copy), tiled and chained self-scheduled forms and keeps the
+fastest, recording it on the plan.
 Results are cached per matrix signature for the process.
 """
 from __future__ import annotations
@@ -82,7 +83,7 @@ def tune(plan, b, x=None, algo="self", lanes=LANES, blocks=BLOCKS, grids=GRID_FR
         for w in lanes:
             run(w, default_block, first_grid, tile0, order)
     w_best, order_best = min(table, key=lambda r: r[3])[0], min(table, key=lambda r: r[3])[5]
-    if algo in ("self", "tiled", "chains"):
+    if algo in ("self", "tiled", "chains", "permuted"):
         for blk in blocks:
             for frac in grids:
                 if (blk, frac * sms) != (default_block, first_grid):
@@ -105,15 +106,15 @@ def _apply(plan, best, algo):
         plan.set_tiling(best[4], best[5])
 
 
-def tune_algos(plan, b, x=None, algos=("self", "tiled", "chains"), reps=3, use_cache=True,
-               **kw):
+def tune_algos(plan, b, x=None, algos=("self", "permuted", "tiled", "chains"), reps=3,
+               use_cache=True, **kw):
     """Tune each self-scheduled form and keep the faster one.
 
     Returns ``{"algo": name, "best": ..., "per_algo": {name: tune(...)}}`` and
     sets ``plan.best_algo`` (used by ``plan.solve(..., algo="auto")``)."""
     nrhs = 1 if b.dim() == 1 else b.shape[1]
     if nrhs > 1:
-        algos = tuple(a for a in algos if a not in ("tiled", "chains")) or ("self",)
+        algos = tuple(a for a in algos if a not in ("tiled", "chains", "permuted")) or ("self",)
     per = {}
     for a in algos:
         if a == "tiled" and not kw:

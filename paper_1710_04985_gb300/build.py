@@ -19,7 +19,8 @@ OUT = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 
 SOURCES = ["api.cu", "analysis.cu", "solve_self.cu", "solve_level.cu", "solve_mrhs.cu", "aux.cu",
-           "solve_tiled.cu", "solve_chain.cu", "noalloc.cu"]
+           "solve_tiled.cu", "solve_chain.cu", "noalloc.cu", "permute.cu",
+           "solve_column.cu", "kahn.cu"]
 CUSPARSE_SOURCES = ["cusparse_ref.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -45,6 +45,17 @@ struct Levels {
     // (built on first use) and the number of segment levels.
     int* torder[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     int nslev[6] = {0, 0, 0, 0, 0, 0};
+    // Level-ordered copy (SPTRSV_ALGO_SELF_PERMUTED, built on first use):
+    // row k = row jlev[k], columns renumbered to positions, values copied;
+    // xp is the position-ordered publication buffer of its solves.
+    int* pptr = nullptr;
+    int* pidx = nullptr;
+    void* pvals = nullptr;
+    void* xp = nullptr;
+    // Column-wise solve (SPTRSV_ALGO_SELF_COLUMN, built on first use): the
+    // dependency count of every row and the working counters.
+    int* count0 = nullptr;
+    int* count = nullptr;
 };
 
 struct DeviceGuard {
@@ -110,7 +121,8 @@ struct sptrsv_plan_s {
     const int* colidx = nullptr;
     const void* vals = nullptr;
     Levels fwd, trn;
-    bool has_trans = false;
+    bool has_trans = false;     // transposed pattern and its levels
+    bool has_tpattern = false;  // transposed pattern
     int* tptr = nullptr;
     int* tidx = nullptr;
     int* tmap = nullptr;
@@ -143,6 +155,12 @@ void free_levels(Levels& L) {
     cudaFree(L.jlev);
     cudaFree(L.ipos);
     for (int* t : L.torder) cudaFree(t);
+    cudaFree(L.pptr);
+    cudaFree(L.pidx);
+    cudaFree(L.pvals);
+    cudaFree(L.xp);
+    cudaFree(L.count0);
+    cudaFree(L.count);
     L = Levels();
 }
 
@@ -179,14 +197,96 @@ sptrsv_status_t take_status(sptrsv_plan_t P, cudaStream_t s, int* row) {
     return (sptrsv_status_t)(unsigned)(h & 0xffffffffu);
 }
 
-// Level analysis of one pattern (Sec. 4.1): the level sweep, then the
+sptrsv_status_t sweep_levels(sptrsv_plan_t P, const int* ptr, const int* idx, bool upper,
+                             Levels& L, int* nlev_out, cudaStream_t s);
+sptrsv_status_t level_sets(sptrsv_plan_t P, Levels& L, int nlev, cudaStream_t s);
+
+// Levels by Kahn's algorithm (Sec. 4.4.1): dptr/didx is the CSR of the
+// transpose of the system (row i lists the rows that depend on i).  The
+// host-loop form launches once per level and reads the queue end back after
+// each launch; the persistent form runs every level in one cooperative
+// launch.  Writes L.lev (allocated by the caller) and *nlev; synchronises s.
+sptrsv_status_t kahn_levels(sptrsv_plan_t P, const int* ptr, const int* idx, const int* dptr,
+                            const int* didx, bool persistent, Levels& L, int* nlev,
+                            cudaStream_t s) {
+    const int n = P->n;
+    int* scratch = nullptr;
+    // Layout (ints): [0, 2) the 64-bit barrier counter, which must be 8-byte
+    // aligned and so comes first (cudaMalloc returns 256-byte aligned
+    // memory); [2] queue end; [3] level count; then count0, count, queue.
+    CK(cudaMalloc(&scratch, sizeof(int) * (3 * (size_t)n + 4)));
+    unsigned long long* arrivals = (unsigned long long*)scratch;
+    int* qend = scratch + 2;
+    int* nlev_dev = scratch + 3;
+    int* count0 = scratch + 4;
+    int* count = count0 + n;
+    int* queue = count + n;
+    cudaError_t e = cudaMemsetAsync(scratch, 0, 4 * sizeof(int), s);
+    if (e == cudaSuccess) e = launch_column_counts(n, ptr, idx, count0, s);
+    if (e == cudaSuccess) e = launch_kahn_roots(n, count0, count, L.lev, queue, qend, s);
+    int h_last = 0, level = 0;
+    if (e == cudaSuccess && persistent) {
+        const int block = 256;
+        long long grid = (long long)kahn_persistent_blocks_per_sm(block) * P->num_sms;
+        if (grid < 1) grid = 1;
+        e = launch_kahn_persistent(dptr, didx, count, L.lev, queue, qend, n, arrivals, nlev_dev,
+                                   P->status, P->spin.limit, (int)grid, block, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&level, nlev_dev, sizeof(int),
+                                                  cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&h_last, qend, sizeof(int),
+                                                  cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    } else if (e == cudaSuccess) {
+        // the paper's driver: one launch and one copy of the queue end per level
+        e = cudaMemcpyAsync(&h_last, qend, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        int first = 0;
+        while (e == cudaSuccess && h_last > first) {
+            e = launch_kahn_level(dptr, didx, count, L.lev, queue, qend, n, first, h_last, level,
+                                  P->status, P->num_sms * 16, s);
+            int nl = h_last;
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&nl, qend, sizeof(int),
+                                                      cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            first = h_last;
+            h_last = nl;
+            ++level;
+        }
+    }
+    cudaFree(scratch);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int row = -1;
+    ST(take_status(P, s, &row));
+    if (h_last != n || level < 1) return SPTRSV_ERR_INTERNAL;  // every row must be leveled
+    *nlev = level;
+    return SPTRSV_OK;
+}
+
+// Level analysis of one pattern (Sec. 4.1): the levels (sync-free sweep, or
+// Kahn's algorithm given the dependents' structure dptr/didx), then the
 // bucket sort into level sets.  Synchronises s.
 sptrsv_status_t build_levels(sptrsv_plan_t P, const int* ptr, const int* idx, bool upper,
-                             Levels& L, cudaStream_t s) {
+                             Levels& L, cudaStream_t s, int method = SPTRSV_ANALYSIS_SWEEP,
+                             const int* dptr = nullptr, const int* didx = nullptr) {
     const int n = P->n;
     CK(cudaMalloc(&L.lev, sizeof(int) * (size_t)n));
     CK(cudaMemsetAsync(L.lev, 0xff, sizeof(int) * (size_t)n, s));
     CK(cudaMemsetAsync(P->counters, 0, 2 * sizeof(int), s));
+    int nlev = 0;
+    if (method == SPTRSV_ANALYSIS_KAHN_HOST_LOOP || method == SPTRSV_ANALYSIS_KAHN_PERSISTENT) {
+        ST(kahn_levels(P, ptr, idx, dptr, didx, method == SPTRSV_ANALYSIS_KAHN_PERSISTENT, L,
+                       &nlev, s));
+    } else {
+        ST(sweep_levels(P, ptr, idx, upper, L, &nlev, s));
+    }
+    return level_sets(P, L, nlev, s);
+}
+
+// Levels by the sync-free sweep (analysis.cu).  Writes L.lev and *nlev;
+// synchronises s.
+sptrsv_status_t sweep_levels(sptrsv_plan_t P, const int* ptr, const int* idx, bool upper,
+                             Levels& L, int* nlev_out, cudaStream_t s) {
+    const int n = P->n;
     // One lane per ~4 entries of an average row (a chunk), so short rows get a
     // lane each and a ticket holds many consecutive rows; a moderate grid
     // keeps the polling traffic down.
@@ -209,6 +309,16 @@ sptrsv_status_t build_levels(sptrsv_plan_t P, const int* ptr, const int* idx, bo
     CK(cudaMemcpyAsync(&nlev, P->counters + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
     int row = -1;
     ST(take_status(P, s, &row));  // synchronises
+    *nlev_out = nlev;
+    return SPTRSV_OK;
+}
+
+// Level sets from L.lev (Sec. 4.1): histogram, exclusive scan to ilev, a
+// stable radix sort of the rows by level to jlev (ascending rows inside a
+// level), a self-check, and the inverse permutation ipos.  Synchronises s.
+sptrsv_status_t level_sets(sptrsv_plan_t P, Levels& L, int nlev, cudaStream_t s) {
+    const int n = P->n;
+    int row = -1;
     L.nlev = nlev;
     CK(cudaMalloc(&L.ilev, sizeof(int) * (size_t)(nlev + 1)));
     CK(cudaMalloc(&L.jlev, sizeof(int) * (size_t)n));
@@ -252,10 +362,25 @@ sptrsv_status_t build_levels(sptrsv_plan_t P, const int* ptr, const int* idx, bo
 }
 
 // CSR of A^T (the CSC of A, Sec. 3.2) with a value map, and its levels.
+sptrsv_status_t build_transpose_pattern(sptrsv_plan_t P, cudaStream_t s);
 sptrsv_status_t build_transpose(sptrsv_plan_t P, cudaStream_t s) {
     if (P->has_trans) return SPTRSV_OK;
     if (capturing(s)) return SPTRSV_ERR_NOT_SUPPORTED;
+    ST(build_transpose_pattern(P, s));
+    ST(build_levels(P, P->tptr, P->tidx, !P->upper, P->trn, s));
+    P->has_trans = true;
+    return SPTRSV_OK;
+}
+
+// The transposed pattern alone (no levels), built once.
+sptrsv_status_t build_transpose_pattern(sptrsv_plan_t P, cudaStream_t s) {
+    if (P->has_tpattern) return SPTRSV_OK;
+    if (capturing(s)) return SPTRSV_ERR_NOT_SUPPORTED;
     const int n = P->n, nnz = P->nnz;
+    cudaFree(P->tptr);  // left over from a failed attempt, if any
+    cudaFree(P->tidx);
+    cudaFree(P->tmap);
+    P->tptr = P->tidx = P->tmap = nullptr;
     CK(cudaMalloc(&P->tptr, sizeof(int) * (size_t)(n + 1)));
     CK(cudaMalloc(&P->tidx, sizeof(int) * (size_t)(nnz > 0 ? nnz : 1)));
     CK(cudaMalloc(&P->tmap, sizeof(int) * (size_t)(nnz > 0 ? nnz : 1)));
@@ -292,8 +417,7 @@ sptrsv_status_t build_transpose(sptrsv_plan_t P, cudaStream_t s) {
         rc = take_status(P, s, &row);
     }
     if (rc != SPTRSV_OK) return SPTRSV_ERR_INTERNAL;
-    ST(build_levels(P, P->tptr, P->tidx, !P->upper, P->trn, s));
-    P->has_trans = true;
+    P->has_tpattern = true;
     return SPTRSV_OK;
 }
 
@@ -373,6 +497,90 @@ sptrsv_status_t build_chain(sptrsv_plan_t P, bool trans, int lanes, cudaStream_t
     return SPTRSV_OK;
 }
 
+// Level-ordered copy of one direction's pattern and values (Sec. 4.3,
+// remark 2: preordering by level), its self-check and the publication
+// buffer.  Built once per direction; allocates and synchronises s.
+sptrsv_status_t build_permuted(sptrsv_plan_t P, bool trans, cudaStream_t s) {
+    Levels& L = trans ? P->trn : P->fwd;
+    if (L.pptr) return SPTRSV_OK;
+    if (capturing(s)) return SPTRSV_ERR_NOT_SUPPORTED;
+    const int n = P->n, nnz = P->nnz;
+    const size_t esize = P->f64 ? sizeof(double) : sizeof(float);
+    const int* ptr = trans ? P->tptr : P->rowptr;
+    const int* idx = trans ? P->tidx : P->colidx;
+    const int* vmap = trans ? P->tmap : nullptr;
+    int *pptr = nullptr, *pidx = nullptr, *lens = nullptr;
+    void *pvals = nullptr, *xp = nullptr;
+    cudaError_t e = cudaMalloc(&pptr, sizeof(int) * ((size_t)n + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&pidx, sizeof(int) * (nnz > 0 ? (size_t)nnz : 1));
+    if (e == cudaSuccess) e = cudaMalloc(&pvals, esize * (nnz > 0 ? (size_t)nnz : 1));
+    if (e == cudaSuccess) e = cudaMalloc(&xp, esize * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&lens, sizeof(int) * (size_t)n);
+    if (e == cudaSuccess) e = launch_ordered_lengths(n, ptr, L.jlev, lens, s);
+    if (e == cudaSuccess) e = launch_exclusive_scan(lens, pptr, n, s);
+    if (e == cudaSuccess)
+        e = launch_permute_rows(P->f64, n, ptr, idx, vmap, P->vals, L.jlev, L.ipos, pptr, pidx,
+                                pvals, P->num_sms * 16, s);
+    if (e == cudaSuccess) e = launch_verify_permuted(n, pptr, pidx, P->status, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    sptrsv_status_t rc = e == cudaSuccess ? SPTRSV_OK : cuda_fail(e);
+    int row = -1;
+    if (rc == SPTRSV_OK && take_status(P, s, &row) != SPTRSV_OK) rc = SPTRSV_ERR_INTERNAL;
+    cudaFree(lens);
+    if (rc != SPTRSV_OK) {
+        cudaFree(pptr);
+        cudaFree(pidx);
+        cudaFree(pvals);
+        cudaFree(xp);
+        return rc;
+    }
+    L.pptr = pptr;
+    L.pidx = pidx;
+    L.pvals = pvals;
+    L.xp = xp;
+    return SPTRSV_OK;
+}
+
+// Dependency counters of the column-wise solve (Alg. 4) for one direction:
+// count0[r] = off-diagonal entries of row r of the system matrix.  The
+// column structure is the CSR of the system's transpose, so the forward
+// solve needs the transposed pattern too.  Allocates and synchronises s.
+sptrsv_status_t build_column(sptrsv_plan_t P, bool trans, cudaStream_t s) {
+    Levels& L = trans ? P->trn : P->fwd;
+    if (L.count0) return SPTRSV_OK;
+    if (capturing(s)) return SPTRSV_ERR_NOT_SUPPORTED;
+    ST(build_transpose(P, s));
+    int *count0 = nullptr, *count = nullptr;
+    cudaError_t e = cudaMalloc(&count0, sizeof(int) * (size_t)P->n);
+    if (e == cudaSuccess) e = cudaMalloc(&count, sizeof(int) * (size_t)P->n);
+    if (e == cudaSuccess)
+        e = launch_column_counts(P->n, trans ? P->tptr : P->rowptr, trans ? P->tidx : P->colidx,
+                                 count0, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaFree(count0);
+        cudaFree(count);
+        return cuda_fail(e);
+    }
+    L.count0 = count0;
+    L.count = count;
+    return SPTRSV_OK;
+}
+
+// Re-gathers the values of every level-ordered copy from the plan's values.
+cudaError_t refresh_permuted(sptrsv_plan_t P, cudaStream_t s) {
+    for (int d = 0; d < 2; ++d) {
+        Levels& L = d ? P->trn : P->fwd;
+        if (!L.pvals) continue;
+        cudaError_t e = launch_permute_rows(P->f64, P->n, d ? P->tptr : P->rowptr,
+                                            d ? P->tidx : P->colidx, d ? P->tmap : nullptr,
+                                            P->vals, L.jlev, L.ipos, L.pptr, nullptr, L.pvals,
+                                            P->num_sms * 16, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 sptrsv_status_t ensure_bytes(void** buf, size_t* have, size_t want, cudaStream_t s) {
     if (*have >= want) return SPTRSV_OK;
     if (capturing(s)) return SPTRSV_ERR_NOT_SUPPORTED;
@@ -413,6 +621,11 @@ sptrsv_status_t run_solve(sptrsv_plan_t P, bool trans, bool f64, const void* val
     const bool mrhs = nrhs > 1;
     const int lanes = mrhs ? mrhs_lanes(nrhs) : P->lanes;
     if (algo == SPTRSV_ALGO_SELF_CHAINS && !mrhs) ST(build_chain(P, trans, lanes, s));
+    // the level-ordered copy holds the plan's own element type
+    const bool permuted = algo == SPTRSV_ALGO_SELF_PERMUTED && !mrhs && f64 == P->f64;
+    if (permuted) ST(build_permuted(P, trans, s));
+    const bool column = algo == SPTRSV_ALGO_SELF_COLUMN && !mrhs;
+    if (column) ST(build_column(P, trans, s));
     const Levels& L = trans ? P->trn : P->fwd;
     SolveParams p;
     memset(&p, 0, sizeof(p));
@@ -445,6 +658,52 @@ sptrsv_status_t run_solve(sptrsv_plan_t P, bool trans, bool f64, const void* val
         }
         ST(prof_end(P, s));
         launches = L.nlev;
+    } else if (column) {
+        // Alg. 4: the column structure of the system is the CSR of its
+        // transpose: the plan's transposed pattern for a forward solve, the
+        // caller's CSR for a transposed one.
+        ColumnParams c;
+        c.ptr = trans ? P->rowptr : P->tptr;
+        c.idx = trans ? P->colidx : P->tidx;
+        c.vmap = trans ? nullptr : P->tmap;
+        c.diag_first = trans ? P->upper : !P->upper;  // a lower system
+        c.count = L.count;
+        c.count0 = L.count0;
+        CK(launch_prep_column(f64, p, c, P->num_sms * 8, s));
+        const int R = 32 / lanes;
+        const long long tickets = ((long long)P->n + R - 1) / R;
+        const long long want_blocks = (tickets + P->block / 32 - 1) / (P->block / 32);
+        long long grid =
+            (long long)column_blocks_per_sm(f64, lanes, c.vmap != nullptr, P->block) * P->num_sms;
+        if (P->max_blocks > 0 && grid > P->max_blocks) grid = P->max_blocks;
+        if (grid > want_blocks) grid = want_blocks;
+        if (grid < 1) grid = 1;
+        ST(prof_begin(P, s));
+        CK(launch_column_k1(f64, lanes, p, c, (int)grid, P->block, s));
+        ST(prof_end(P, s));
+        launches = 2;
+    } else if (permuted) {
+        // Rows publish to the position-ordered buffer L.xp and store x(i) for
+        // the caller; b(i) is read once, by row i, before x(i) is written, so
+        // an in-place solve needs no copy of b.
+        p.ptr = L.pptr;
+        p.idx = L.pidx;
+        p.vmap = nullptr;
+        p.vals = L.pvals;
+        p.xp = L.xp;
+        CK(launch_prep_self(f64, P->n, 1, L.xp, 1, nullptr, 0, nullptr, P->counters,
+                            P->num_sms * 8, s));
+        const int R = 32 / lanes;
+        const long long tickets = ((long long)P->n + R - 1) / R;
+        const long long want_blocks = (tickets + P->block / 32 - 1) / (P->block / 32);
+        long long grid = (long long)self_perm_blocks_per_sm(f64, lanes, P->block) * P->num_sms;
+        if (P->max_blocks > 0 && grid > P->max_blocks) grid = P->max_blocks;
+        if (grid > want_blocks) grid = want_blocks;
+        if (grid < 1) grid = 1;
+        ST(prof_begin(P, s));
+        CK(launch_self_k1(f64, lanes, p, (int)grid, P->block, s));
+        ST(prof_end(P, s));
+        launches = 2;
     } else {
         const size_t esize = f64 ? sizeof(double) : sizeof(float);
         void* bcopy = nullptr;
@@ -499,7 +758,8 @@ sptrsv_status_t solve_common(sptrsv_plan_t P, bool trans, const void* b, void* x
                              int ld, sptrsv_algo_t algo, void* stream) {
     if (!P || nrhs < 1 || ld < nrhs ||
         (algo != SPTRSV_ALGO_LEVEL && algo != SPTRSV_ALGO_SELF && algo != SPTRSV_ALGO_SELF_TILED &&
-         algo != SPTRSV_ALGO_SELF_CHAINS))
+         algo != SPTRSV_ALGO_SELF_CHAINS && algo != SPTRSV_ALGO_SELF_PERMUTED &&
+         algo != SPTRSV_ALGO_SELF_COLUMN))
         return SPTRSV_ERR_INVALID_ARG;
     P->last_launches = 0;
     if (P->n == 0) return SPTRSV_OK;
@@ -578,6 +838,55 @@ sptrsv_status_t sptrsv_analyze(int n, int nnz, const int* d_rowptr, const int* d
     return SPTRSV_OK;
 }
 
+sptrsv_status_t sptrsv_reanalyze(sptrsv_plan_t plan, int transpose, sptrsv_analysis_t method,
+                                 void* stream) {
+    if (!plan || (transpose != 0 && transpose != 1) ||
+        (method != SPTRSV_ANALYSIS_SWEEP && method != SPTRSV_ANALYSIS_KAHN_HOST_LOOP &&
+         method != SPTRSV_ANALYSIS_KAHN_PERSISTENT))
+        return SPTRSV_ERR_INVALID_ARG;
+    sptrsv_plan_t P = plan;
+    if (P->n == 0) return SPTRSV_OK;
+    DeviceGuard g(P->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (capturing(s)) return SPTRSV_ERR_NOT_SUPPORTED;
+    if (transpose) ST(build_transpose(P, s));
+    CK(cudaStreamSynchronize(s));
+    const auto t0 = std::chrono::steady_clock::now();
+    const bool kahn = method != SPTRSV_ANALYSIS_SWEEP;
+    // Kahn's algorithm walks the outgoing edges: the transposed pattern for
+    // the forward system (built here if needed, as Table 1's TRANS_GPU), the
+    // caller's CSR for the transposed one.
+    if (kahn && !transpose) ST(build_transpose_pattern(P, s));
+    Levels& L = transpose ? P->trn : P->fwd;
+    Levels fresh;
+    const int* ptr = transpose ? P->tptr : P->rowptr;
+    const int* idx = transpose ? P->tidx : P->colidx;
+    const bool upper = transpose ? !P->upper : P->upper;
+    sptrsv_status_t rc = build_levels(P, ptr, idx, upper, fresh, s, method,
+                                      transpose ? P->rowptr : P->tptr,
+                                      transpose ? P->colidx : P->tidx);
+    if (rc != SPTRSV_OK) {
+        free_levels(fresh);
+        return rc;
+    }
+    P->analysis_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    (void)kahn;
+    // Levels are unique, so data derived from them stay valid; keep the
+    // segment orders and counters, rebuild the level-ordered copy lazily.
+    for (int k = 0; k < 6; ++k) {
+        fresh.torder[k] = L.torder[k];
+        fresh.nslev[k] = L.nslev[k];
+        L.torder[k] = nullptr;
+    }
+    fresh.count0 = L.count0;
+    fresh.count = L.count;
+    L.count0 = L.count = nullptr;
+    free_levels(L);
+    L = std::move(fresh);
+    return SPTRSV_OK;
+}
+
 sptrsv_status_t sptrsv_free(sptrsv_plan_t plan) {
     if (!plan) return SPTRSV_ERR_INVALID_ARG;
     {
@@ -634,10 +943,12 @@ sptrsv_status_t sptrsv_residual(sptrsv_plan_t plan, const double* d_b, const dou
 
 sptrsv_status_t sptrsv_refresh_values(sptrsv_plan_t plan, void* stream) {
     if (!plan) return SPTRSV_ERR_INVALID_ARG;
-    if (!plan->vals32 || plan->nnz == 0) return SPTRSV_OK;
+    if (plan->nnz == 0) return SPTRSV_OK;
     DeviceGuard g(plan->device);
-    CK(launch_to_f32(plan->nnz, 1, (const double*)plan->vals, 1, plan->vals32, nullptr,
-                     plan->num_sms * 16, (cudaStream_t)stream));
+    if (plan->vals32)
+        CK(launch_to_f32(plan->nnz, 1, (const double*)plan->vals, 1, plan->vals32, nullptr,
+                         plan->num_sms * 16, (cudaStream_t)stream));
+    CK(refresh_permuted(plan, (cudaStream_t)stream));
     return SPTRSV_OK;
 }
 

@@ -31,6 +31,20 @@ struct SolveParams {
     const int* ipos;      // tiled solve in level order: position of each row in jlev
                           // (nullptr: tiles follow the substitution order)
     int kbeg, cnt;        // level-scheduled: this launch's slice of jlev
+    void* xp;             // level-ordered solve: publication buffer in position
+                          // order (nullptr: rows publish to x itself)
+};
+
+// Column structure of the column-wise solve (solve_column.cu): the CSR of
+// the transpose of the system matrix, so row i lists the unknowns that
+// depend on unknown i, plus the dependency counters.
+struct ColumnParams {
+    const int* ptr;
+    const int* idx;
+    const int* vmap;      // nullptr: entry q has value vals[q]
+    int diag_first;       // the diagonal is a row's first entry (a lower system)
+    int* count;           // working counters, reset from count0 before each solve
+    const int* count0;    // off-diagonal entries of each row of the system
 };
 
 // ---- solve kernels (solve_self.cu, solve_level.cu, solve_mrhs.cu)
@@ -57,6 +71,31 @@ int tiled_blocks_per_sm(bool f64, int lanes, bool map, int block, int tile_rows)
 cudaError_t launch_chain_k1(bool f64, int lanes, const SolveParams& p, const int* torder,
                             int grid, int block, cudaStream_t s);
 int chain_blocks_per_sm(bool f64, int lanes, bool map, int block);
+// Column-wise self-scheduled solve (Alg. 4, solve_column.cu).  The prep
+// launch sets x = b (unless x == b), count = count0 and the ticket to 0.
+cudaError_t launch_column_counts(int n, const int* ptr, const int* idx, int* count,
+                                 cudaStream_t s);
+cudaError_t launch_prep_column(bool f64, const SolveParams& p, const ColumnParams& c, int grid,
+                               cudaStream_t s);
+cudaError_t launch_column_k1(bool f64, int lanes, const SolveParams& p, const ColumnParams& c,
+                             int grid, int block, cudaStream_t s);
+int column_blocks_per_sm(bool f64, int lanes, bool cmap, int block);
+// Resident blocks per SM of the level-ordered-copy form of self_solve_k1.
+int self_perm_blocks_per_sm(bool f64, int lanes, int block);
+
+// ---- level-ordered copy (permute.cu)
+// lens[k] = length of row jlev[k].
+cudaError_t launch_ordered_lengths(int n, const int* ptr, const int* jlev, int* lens,
+                                   cudaStream_t s);
+// Row k of the copy = row jlev[k] in entry order: pidx = ipos[idx] (skipped
+// when pidx is nullptr, a values-only refresh), pvals = vals[vmap[q] or q].
+cudaError_t launch_permute_rows(bool f64, int n, const int* ptr, const int* idx, const int* vmap,
+                                const void* vals, const int* jlev, const int* ipos,
+                                const int* pptr, int* pidx, void* pvals, int grid,
+                                cudaStream_t s);
+// Self-check: every entry of row k names k or an earlier position.
+cudaError_t launch_verify_permuted(int n, const int* pptr, const int* pidx,
+                                   unsigned long long* status, cudaStream_t s);
 
 // ---- analysis kernels (analysis.cu)
 cudaError_t launch_validate(int n, int nnz, const int* ptr, const int* idx, const void* vals,
@@ -103,6 +142,19 @@ cudaError_t launch_inverse_perm(const int* perm, int n, int* ipos, cudaStream_t 
 // ilev[0] = 0 and ilev[nlev] = n.  Failures are reported as internal.
 cudaError_t launch_verify_levels(int n, int nlev, const int* lev, const int* ilev,
                                  const int* jlev, unsigned long long* status, cudaStream_t s);
+
+// ---- Kahn's algorithm (kahn.cu, Sec. 4.4.1); dptr/didx: CSR of the
+// transpose of the system (the outgoing edges of every row)
+cudaError_t launch_kahn_roots(int n, const int* count0, int* count, int* lev, int* queue,
+                              int* qend, cudaStream_t s);
+cudaError_t launch_kahn_level(const int* dptr, const int* didx, int* count, int* lev, int* queue,
+                              int* qend, int n, int first, int last, int level,
+                              unsigned long long* status, int max_grid, cudaStream_t s);
+int kahn_persistent_blocks_per_sm(int block);
+cudaError_t launch_kahn_persistent(const int* dptr, const int* didx, int* count, int* lev,
+                                   int* queue, int* qend, int n, unsigned long long* arrivals,
+                                   int* nlev_out, unsigned long long* status, long long limit,
+                                   int grid, int block, cudaStream_t s);
 
 // ---- auxiliary kernels (aux.cu)
 cudaError_t launch_grad_vals(bool f64, int lanes, int n, const int* ptr, const int* idx, bool unit,

@@ -59,7 +59,15 @@ cudaError_t launch_prep_self(bool f64, int n, int nrhs, void* x, long long ldx, 
 }
 
 
-template <typename T, int W, bool MAP>
+// PERM: the pattern is the plan's level-ordered copy (SPTRSV_ALGO_SELF_PERMUTED):
+// row position k of jlev holds the entries of row jlev[k] in their original
+// order, with column indices renumbered to positions and the values copied
+// alongside (p.ptr, p.idx, p.vals), so a warp's rows and the unknowns they
+// wait on are contiguous.  Results are published in p.xp (position order,
+// the array that is polled) and stored to x(jlev[k]) for the caller.  The
+// arithmetic and its order are those of the unpermuted kernel, so both give
+// bitwise identical results for the same sub-warp width.
+template <typename T, int W, bool MAP, bool PERM>
 __global__ void __launch_bounds__(1024) self_solve_k1(SolveParams p) {
     constexpr int R = 32 / W;
     constexpr int E = kChunk;
@@ -71,6 +79,8 @@ __global__ void __launch_bounds__(1024) self_solve_k1(SolveParams p) {
     const T* __restrict__ vals = (const T*)p.vals;
     const T* b = (const T*)p.b;
     T* x = (T*)p.x;
+    T* xpub = PERM ? (T*)p.xp : x;  // the array rows publish to and wait on
+    const long long ldp = PERM ? 1 : p.ldx;
     int t = 0;
     if (lane == 0) t = atomicAdd(p.ticket, 1);
     t = __shfl_sync(FULL, t, 0);
@@ -81,10 +91,12 @@ __global__ void __launch_bounds__(1024) self_solve_k1(SolveParams p) {
         const bool has_row = k < p.n;
         int i = 0, beg = 0, end = 0;
         T dinv = T(1), sum = T(0);
+        // identity of the row inside the pattern: its own column index
+        const int self_col = PERM ? (int)k : 0;
         if (has_row) {
             i = p.jlev[k];
-            beg = p.ptr[i];
-            end = p.ptr[i + 1];
+            beg = p.ptr[PERM ? k : i];
+            end = p.ptr[(PERM ? k : i) + 1];
             if (sl == 0) {
                 // Everything that does not depend on x happens now, while the
                 // dependencies are pending (SLFR computes 1/d(i) up front too):
@@ -115,7 +127,7 @@ __global__ void __launch_bounds__(1024) self_solve_k1(SolveParams p) {
                 v[e] = T(0);
                 if (q < end) {
                     const int cc = p.idx[q];
-                    if (cc != i) {
+                    if (cc != (PERM ? self_col : i)) {
                         c[e] = cc;
                         a[e] = vals[MAP ? p.vmap[q] : q];
                         live |= 1u << e;
@@ -124,7 +136,7 @@ __global__ void __launch_bounds__(1024) self_solve_k1(SolveParams p) {
             }
 #pragma unroll
             for (int e = 0; e < E; ++e)
-                if (live & (1u << e)) v[e] = ld_relaxed(x + (long long)c[e] * p.ldx);
+                if (live & (1u << e)) v[e] = ld_relaxed(xpub + (long long)c[e] * ldp);
             if (!p.unit) {
 #pragma unroll
                 for (int e = 0; e < E; ++e)
@@ -150,8 +162,11 @@ __global__ void __launch_bounds__(1024) self_solve_k1(SolveParams p) {
             const bool fresh = !published && (done & gmask) == gmask;
             if (__any_sync(FULL, fresh)) {  // FP64 is scarce on GB300: reduce only then
                 const T tot = group_sum<W>(sum, FULL);
-                if (fresh && sl == 0 && i != p.withhold)
-                    st_relaxed(x + (long long)i * p.ldx, publishable(tot));
+                if (fresh && sl == 0 && i != p.withhold) {
+                    const T val = publishable(tot);
+                    st_relaxed(xpub + (PERM ? k : (long long)i * p.ldx), val);
+                    if (PERM) x[(long long)i * p.ldx] = val;
+                }
             }
             published = published || fresh;
             if (__all_sync(FULL, published)) break;
@@ -167,7 +182,7 @@ __global__ void __launch_bounds__(1024) self_solve_k1(SolveParams p) {
                 do {
 #pragma unroll
                     for (int e = 0; e < E; ++e)
-                        if (pend & (1u << e)) v[e] = ld_relaxed(x + (long long)c[e] * p.ldx);
+                        if (pend & (1u << e)) v[e] = ld_relaxed(xpub + (long long)c[e] * ldp);
 #pragma unroll
                     for (int e = 0; e < E; ++e)
                         if ((pend & (1u << e)) && !Marker<T>::pending(v[e])) pend &= ~(1u << e);
@@ -199,10 +214,12 @@ __global__ void __launch_bounds__(1024) self_solve_k1(SolveParams p) {
 
 template <typename T, int W>
 static cudaError_t self_w(const SolveParams& p, int grid, int block, cudaStream_t s) {
-    if (p.vmap)
-        self_solve_k1<T, W, true><<<grid, block, 0, s>>>(p);
+    if (p.xp)  // level-ordered copy: values already gathered, no map
+        self_solve_k1<T, W, false, true><<<grid, block, 0, s>>>(p);
+    else if (p.vmap)
+        self_solve_k1<T, W, true, false><<<grid, block, 0, s>>>(p);
     else
-        self_solve_k1<T, W, false><<<grid, block, 0, s>>>(p);
+        self_solve_k1<T, W, false, false><<<grid, block, 0, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -229,14 +246,36 @@ static int occ_k1(int lanes, int block) {
     int nb = 0;
     cudaError_t e = cudaErrorInvalidValue;
     switch (lanes) {
-        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, self_solve_k1<T, 1, MAP>, block, 0); break;
-        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, self_solve_k1<T, 2, MAP>, block, 0); break;
-        case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, self_solve_k1<T, 4, MAP>, block, 0); break;
-        case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, self_solve_k1<T, 8, MAP>, block, 0); break;
-        case 16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, self_solve_k1<T, 16, MAP>, block, 0); break;
-        case 32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, self_solve_k1<T, 32, MAP>, block, 0); break;
+        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, self_solve_k1<T, 1, MAP, false>, block, 0); break;
+        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, self_solve_k1<T, 2, MAP, false>, block, 0); break;
+        case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, self_solve_k1<T, 4, MAP, false>, block, 0); break;
+        case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, self_solve_k1<T, 8, MAP, false>, block, 0); break;
+        case 16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, self_solve_k1<T, 16, MAP, false>, block, 0); break;
+        case 32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, self_solve_k1<T, 32, MAP, false>, block, 0); break;
     }
     return (e == cudaSuccess && nb > 0) ? nb : 1;
+}
+
+template <typename T>
+static int occ_perm(int lanes, int block) {
+    int nb = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+#define SPTRSV_OCC(WW) \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, self_solve_k1<T, WW, false, true>, block, 0)
+    switch (lanes) {
+        case 1: SPTRSV_OCC(1); break;
+        case 2: SPTRSV_OCC(2); break;
+        case 4: SPTRSV_OCC(4); break;
+        case 8: SPTRSV_OCC(8); break;
+        case 16: SPTRSV_OCC(16); break;
+        case 32: SPTRSV_OCC(32); break;
+    }
+#undef SPTRSV_OCC
+    return (e == cudaSuccess && nb > 0) ? nb : 1;
+}
+
+int self_perm_blocks_per_sm(bool f64, int lanes, int block) {
+    return f64 ? occ_perm<double>(lanes, block) : occ_perm<float>(lanes, block);
 }
 
 int self_k1_blocks_per_sm(bool f64, int lanes, bool map, int block) {

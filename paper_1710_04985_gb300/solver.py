@@ -15,7 +15,8 @@ from . import _lib
 from ._lib import SptrsvError, check
 
 ALGOS = {"level": _lib.ALGO_LEVEL, "self": _lib.ALGO_SELF, "tiled": _lib.ALGO_SELF_TILED,
-         "chains": _lib.ALGO_SELF_CHAINS}
+         "chains": _lib.ALGO_SELF_CHAINS, "permuted": _lib.ALGO_SELF_PERMUTED,
+         "column": _lib.ALGO_SELF_COLUMN}
 
 
 def _ptr(t):
@@ -198,6 +199,17 @@ class TriangularPlan:
     def refresh_values(self, stream=None):
         check(_lib.load().sptrsv_refresh_values(self._h, _stream_handle(stream)),
               "sptrsv_refresh_values")
+
+    ANALYSIS = {"sweep": _lib.ANALYSIS_SWEEP, "kahn_host_loop": _lib.ANALYSIS_KAHN_HOST_LOOP,
+                "kahn_persistent": _lib.ANALYSIS_KAHN_PERSISTENT}
+
+    def reanalyze(self, method="sweep", transpose=False, stream=None):
+        """Recompute the levels of the forward (or transposed) system with
+        ``method`` ("sweep", "kahn_host_loop" as in Sec. 4.4.1,
+        "kahn_persistent"); returns the analysis time in ms."""
+        check(_lib.load().sptrsv_reanalyze(self._h, int(bool(transpose)), self.ANALYSIS[method],
+                                           _stream_handle(stream)), "sptrsv_reanalyze")
+        return self.analysis_ms
 
     # ------------------------------------------------------------ tuning
     def set_tuning(self, lanes_per_row, block_size=256, max_blocks=0):

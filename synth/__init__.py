@@ -18,6 +18,9 @@ Workloads (seeds are ``SEED_BASE + k`` for workload k):
                          SuiteSparse/MFEM matrices of Sec. 5.2 (Table 3), which
                          are not available: Pareto row lengths, banded plus
                          uniform column draws, diagonally dominant values.
+* ``laplacian_triangles`` lower and upper triangles (diagonal included) of the
+                         5/9-point 2-D and 7/27-point 3-D Laplacians on the
+                         regular grids of Table 2 (Sec. 5.1).
 * ``block_diagonal``     many independent systems concatenated into one.
 """
 from __future__ import annotations
@@ -172,6 +175,51 @@ def lap3d_7pt_lower(nx: int, ny: int, nz: int) -> CSR:
     vals = np.where(rows == cols, 6.0, -1.0)
     return _from_sorted_coo(n, rows, cols, vals, name=f"lap3d_7pt_lower_{nx}x{ny}x{nz}",
                             meta={"grid": (nx, ny, nz)})
+
+
+def _full_stencil(ndim: int):
+    """Every displacement in {-1, 0, 1}^ndim: the 9-point (2-D) and 27-point
+    (3-D) stencils of Sec. 5.1, diagonal included."""
+    grids = np.indices((3,) * ndim).reshape(ndim, -1).T - 1
+    return [tuple(int(v) for v in g) for g in grids]
+
+
+STENCILS = {
+    (2, 5): _FIVE_POINT,
+    (2, 9): _full_stencil(2),
+    (3, 7): _SEVEN_POINT,
+    (3, 27): _full_stencil(3),
+}
+
+
+def laplacian_triangles(dims, points: int):
+    """``(L + D, U + D)`` of the ``points``-point Laplacian on a regular grid
+    ``dims = (nx, ny)`` or ``(nx, ny, nz)`` in lexicographic order (x
+    fastest), the test problems of Sec. 5.1 (Table 2) split as in eq. (3):
+    A = L + D + U.  Every neighbour entry is -1 and the diagonal is
+    ``points - 1`` (the number of neighbours of an interior point), so A is
+    the graph Laplacian of the stencil: 4/-1 for 5 points, 8/-1 for 9,
+    6/-1 for 7 and 26/-1 for 27."""
+    dims = tuple(int(d) for d in dims)
+    offsets = STENCILS[(len(dims), int(points))]
+    diag = float(points - 1)
+    tag = "x".join(str(d) for d in dims)
+    out = []
+    for upper in (False, True):
+        n, rows, cols, _ = _stencil_triangle(dims, offsets, upper=upper)
+        vals = np.where(rows == cols, diag, -1.0)
+        out.append(_from_sorted_coo(n, rows, cols, vals, upper=upper,
+                                    name=f"lap{len(dims)}d_{points}pt_"
+                                         f"{'upper' if upper else 'lower'}_{tag}",
+                                    meta={"grid": dims, "points": int(points)}))
+    return out[0], out[1]
+
+
+# Regular grids of Table 2 (Sec. 5.1): n = 2^20 in 2-D and 2^21 in 3-D, with
+# growing aspect ratios rho_yx = ny/nx and rho_zx = nz/nx (eq. (5)).
+TABLE2_GRIDS_2D = [(1024, 1024), (512, 2048), (256, 4096), (128, 8192), (64, 16384)]
+TABLE2_GRIDS_3D = [(128, 128, 128), (64, 128, 256), (64, 64, 512), (32, 64, 1024),
+                   (32, 32, 2048)]
 
 
 def general_lower(n: int, seed: int, band: int = 512, p_band: float = 0.7,

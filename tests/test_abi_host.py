@@ -72,6 +72,7 @@ def test_host_argument_checks_without_gpu(lib):
     assert lib.sptrsv_set_tuning(None, 4, 256, 0) == 1
     assert lib.sptrsv_set_spin_limit(None, 10) == 1
     assert lib.sptrsv_free(None) == 1
+    assert lib.sptrsv_reanalyze(None, 0, 1, None) == 1
     assert lib.sptrsv_last_launch_count(None) == 0
 
 

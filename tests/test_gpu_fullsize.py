@@ -41,7 +41,7 @@ def test_workload1_ilu_factors_forward_and_backward(w1):
             assert_levels_equal(p.levels(), A)
             assert p.levels()["nlev"] == 382
             bt = torch.tensor(b, device=dev())
-            for algo in ("auto", "self", "tiled", "level"):
+            for algo in ("auto", "self", "permuted", "tiled", "level"):
                 assert relerr(p.solve(bt, algo=algo), ref) <= TOL64
             assert relerr(ref, xt) <= 1e-10           # manufactured solution recovered
             assert p.status() == (0, -1)
@@ -84,7 +84,7 @@ def test_workload2_general_fp64_fp32(w2):
     with bench_plan(A, b) as p:
         assert_levels_equal(p.levels(), A)
         bt = torch.tensor(b, device=dev())
-        for algo in ("auto", "self", "tiled", "level"):
+        for algo in ("auto", "self", "permuted", "tiled", "level"):
             assert relerr(p.solve(bt, algo=algo), ref) <= TOL64
     with bench_plan(A, b, torch.float32) as p32:
         x32 = p32.solve(torch.tensor(b, device=dev(), dtype=torch.float32), algo="auto")
@@ -92,6 +92,28 @@ def test_workload2_general_fp64_fp32(w2):
     with plan_for(A) as p:
         x, iters, rel = p.solve_refined(torch.tensor(b, device=dev()))
         assert relerr(x, ref) <= TOL64
+
+
+@pytest.mark.parametrize("dims,pts", [((1024, 1024), 9), ((128, 128, 128), 27),
+                                      ((64, 16384), 5), ((32, 32, 2048), 7)])
+def test_table2_stencil_pair(dims, pts):
+    """Sec. 5.1 at full size: the solve pair of eq. (3) on Table 2 grids, in
+    the launch configuration the sweep times (autotuned), against the oracle
+    and the manufactured solution; levels bit-exact."""
+    L, U = synth.laplacian_triangles(dims, pts)
+    xt = synth.uniform(L.n, synth.SEED_BASE + 10 + pts)
+    b = synth.times_vector(L, synth.times_vector(U, xt))
+    c = oracle.solve(L.rowptr, L.colidx, L.vals, b)
+    ref = oracle.solve(U.rowptr, U.colidx, U.vals, c, upper=True)
+    assert relerr(ref, xt) <= 1e-10
+    with bench_plan(L, b) as pl:
+        assert_levels_equal(pl.levels(), L)
+        y = pl.solve(torch.tensor(b, device=dev()), algo="auto")
+        assert relerr(y, c) <= TOL64
+        with bench_plan(U, c) as pu:
+            assert_levels_equal(pu.levels(), U)
+            for algo in ("auto", "self", "permuted"):
+                assert relerr(pu.solve(y, algo=algo), ref) <= TOL64
 
 
 def test_workload4_gradient(w2):

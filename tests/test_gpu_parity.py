@@ -34,6 +34,11 @@ MATRICES = {
     "long_rows": long_rows,
     "unit_nodiag": unit_without_diagonal,
     "lap2d_upper": lambda: synth.lap2d_5pt_upper(37, 29),
+    # the 9- and 27-point stencils of Sec. 5.1 (Table 2), both triangles
+    "lap2d_9pt": lambda: synth.laplacian_triangles((37, 29), 9)[0],
+    "lap2d_9pt_upper": lambda: synth.laplacian_triangles((37, 29), 9)[1],
+    "lap3d_27pt": lambda: synth.laplacian_triangles((13, 11, 9), 27)[0],
+    "lap3d_27pt_upper": lambda: synth.laplacian_triangles((13, 11, 9), 27)[1],
 }
 
 _cache = {}
@@ -74,9 +79,33 @@ def test_transpose_levels_and_pattern(name):
         assert np.array_equal(A.vals[tmap], T.data)
 
 
+@pytest.mark.parametrize("method", ["kahn_host_loop", "kahn_persistent", "sweep"])
+@pytest.mark.parametrize("name", ["workload0", "ilu_L", "ilu_U", "general", "general_upper",
+                                  "bidiag", "diag", "long_rows", "unit_nodiag", "lap3d_27pt"])
+def test_reanalyze_methods_give_the_same_levels(name, method):
+    """Sec. 4.4.1: Kahn's algorithm (host loop as in the paper, or one
+    persistent launch) and the sync-free sweep give the same (unique) levels
+    and level sets, forward and transposed, and solves stay exact."""
+    A = mat(name)
+    b = synth.uniform(A.n, 25)
+    with plan_for(A) as p:
+        assert p.reanalyze(method) > 0
+        assert_levels_equal(p.levels(), A)
+        bt = torch.tensor(b, device=dev())
+        ref = oracle.solve(A.rowptr, A.colidx, A.vals, b, upper=A.upper, unit=A.unit)
+        for algo in ("self", "permuted", "level"):
+            assert relerr(p.solve(bt, algo=algo), ref) <= TOL64
+        p.reanalyze(method, transpose=True)
+        assert_levels_equal(p.levels(transpose=True), A, transpose=True)
+        reft = oracle.solve_transpose(A.rowptr, A.colidx, A.vals, b, upper=A.upper, unit=A.unit)
+        assert relerr(p.solve_transpose(bt), reft) <= TOL64
+        assert p.status() == (0, -1)
+
+
 # ---------------------------------------------------------------- solves
 
-@pytest.mark.parametrize("algo", ["self", "level", "tiled", "tiled_levels", "chains"])
+@pytest.mark.parametrize("algo", ["self", "level", "tiled", "tiled_levels", "chains", "permuted",
+                                  "column"])
 @pytest.mark.parametrize("name", list(MATRICES))
 def test_solve_fp64(name, algo):
     A = mat(name)
@@ -91,7 +120,7 @@ def test_solve_fp64(name, algo):
         assert p.status() == (0, -1)
 
 
-@pytest.mark.parametrize("algo", ["self", "level", "tiled", "chains"])
+@pytest.mark.parametrize("algo", ["self", "level", "tiled", "chains", "permuted", "column"])
 @pytest.mark.parametrize("name", ["general", "ilu_L", "ilu_U", "long_rows"])
 def test_solve_fp32(name, algo):
     A = mat(name)
@@ -111,11 +140,13 @@ def test_every_launch_shape(lanes, block):
     with plan_for(A) as p:
         p.set_tuning(lanes, block, 0)
         bt = torch.tensor(b, device=dev())
-        for algo in ("self", "level", "chains"):
+        for algo in ("self", "level", "chains", "permuted", "column"):
             assert relerr(p.solve(bt, algo=algo), ref) <= TOL64
         p.set_tuning(lanes, block, 3)          # a tiny persistent grid still finishes
         assert relerr(p.solve(bt), ref) <= TOL64
         assert relerr(p.solve(bt, algo="chains"), ref) <= TOL64
+        assert relerr(p.solve(bt, algo="permuted"), ref) <= TOL64
+        assert relerr(p.solve(bt, algo="column"), ref) <= TOL64
         for order in (False, True):            # tiled form: ragged and largest tiles
             for tile in (32, 100, 2048, 6112):
                 p.set_tiling(tile, order)
@@ -134,7 +165,7 @@ def test_multi_rhs(k, algo):
             assert relerr(x, ref) <= TOL64
 
 
-@pytest.mark.parametrize("algo", ["self", "level", "tiled", "chains"])
+@pytest.mark.parametrize("algo", ["self", "level", "tiled", "chains", "permuted", "column"])
 def test_leading_dimension_and_in_place(algo):
     A = mat("general")
     k, ld = 3, 5
@@ -155,7 +186,8 @@ def test_leading_dimension_and_in_place(algo):
         assert relerr(v, ref[:, 0]) <= TOL64
 
 
-@pytest.mark.parametrize("algo", ["self", "level", "tiled", "tiled_levels", "chains"])
+@pytest.mark.parametrize("algo", ["self", "level", "tiled", "tiled_levels", "chains", "permuted",
+                                  "column"])
 @pytest.mark.parametrize("name", ["workload0", "ilu_L", "ilu_U", "general", "general_upper",
                                   "long_rows", "unit_nodiag", "bidiag"])
 def test_solve_transpose(name, algo):
@@ -195,6 +227,15 @@ def test_bitwise_determinism_and_algo_agreement():
                 assert torch.equal(p.solve(bt, algo="tiled"), first)
         for _ in range(3):
             assert torch.equal(p.solve(bt, algo="chains"), first)
+        # so does the level-ordered copy, whose rows keep their entry order
+        for _ in range(3):
+            assert torch.equal(p.solve(bt, algo="permuted"), first)
+        tg = torch.tensor(synth.uniform(A.n, 23), device=dev())
+        assert torch.equal(p.solve_transpose(tg, algo="permuted"), p.solve_transpose(tg))
+        # the column-wise form (Alg. 4) adds contributions atomically in
+        # arrival order: equal to rounding only
+        for _ in range(3):
+            assert relerr(p.solve(bt, algo="column"), first.cpu().numpy()) <= 1e-13
 
 
 # ---------------------------------------------------------------- edge cases
@@ -231,6 +272,28 @@ def test_values_change_without_reanalysis():
         p.vals.mul_(2.0)
         ref = oracle.solve(A.rowptr, A.colidx, 2.0 * A.vals, b)
         assert relerr(p.solve(bt), ref) <= TOL64
+
+
+def test_level_ordered_copy_follows_value_updates():
+    """The level-ordered copy is a snapshot of the values: sptrsv_refresh_values
+    (in-place change) and sptrsv_set_values (new array) bring it up to date,
+    for the forward and the transposed copy."""
+    A = mat("ilu_U")
+    with plan_for(A) as p:
+        b = synth.uniform(A.n, 24)
+        bt = torch.tensor(b, device=dev())
+        p.solve(bt, algo="permuted")
+        p.solve_transpose(bt, algo="permuted")
+        p.vals.mul_(2.0)
+        p.refresh_values()
+        ref = oracle.solve(A.rowptr, A.colidx, 2.0 * A.vals, b, upper=True)
+        assert relerr(p.solve(bt, algo="permuted"), ref) <= TOL64
+        v3 = torch.tensor(3.0 * A.vals, device=dev())
+        p.set_values(v3)
+        ref = oracle.solve(A.rowptr, A.colidx, 3.0 * A.vals, b, upper=True)
+        assert relerr(p.solve(bt, algo="permuted"), ref) <= TOL64
+        reft = oracle.solve_transpose(A.rowptr, A.colidx, 3.0 * A.vals, b, upper=True)
+        assert relerr(p.solve_transpose(bt, algo="permuted"), reft) <= TOL64
 
 
 def _bad(n, rows, cols, vals, upper=False, unit=False):
@@ -271,7 +334,7 @@ def test_bad_rowptr():
     assert ei.value.status == 2
 
 
-@pytest.mark.parametrize("algo", ["self", "tiled", "chains"])
+@pytest.mark.parametrize("algo", ["self", "tiled", "chains", "permuted", "column"])
 def test_timeout_is_reported_and_solve_finishes(algo):
     """A row that is never published: every row that depends on it gives up
     after the spin limit, records SPTRSV_ERR_TIMEOUT and publishes NaN; rows
@@ -432,5 +495,5 @@ def test_autotuner_picks_an_algorithm_and_stays_exact():
         bt = torch.tensor(b, device=dev())
         res = autotune.tune_algos(p, bt, use_cache=False, lanes=(2, 8), blocks=(256,),
                                   grids=(0, 2), tiles=(512, 2048))
-        assert res["algo"] in ("self", "tiled", "chains") and p.best_algo == res["algo"]
+        assert res["algo"] in ("self", "permuted", "tiled", "chains") and p.best_algo == res["algo"]
         assert relerr(p.solve(bt, algo="auto"), ref) <= TOL64

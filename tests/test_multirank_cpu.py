@@ -50,3 +50,16 @@ def test_reference_arm_runs_on_rank_zero_only(capsys):
         gpus, steps, warmup = 2, 1, 3
     assert bench.run_reference(Args, world=2, rank=1) is None
     assert capsys.readouterr().out == ""
+
+
+def test_break_even_solve_count():
+    """Sec. 5.2's n_s: the smallest number of solves after which a costlier
+    setup with faster solves has the shorter total time."""
+    import bench
+    assert bench._break_even(10.0, 1.0, 5.0, 2.0) == 6      # 16 < 17, but 15 == 15
+    assert bench._break_even(4.0, 1.0, 5.0, 2.0) == 0       # cheaper setup and faster solves
+    assert bench._break_even(10.0, 3.0, 5.0, 2.0) is None   # never
+    for sa, ta, sb, tb in ((29.0, 0.5, 11.0, 1.0), (57.0, 0.66, 102.0, 2.05)):
+        k = bench._break_even(sa, ta, sb, tb)
+        assert sa + k * ta < sb + k * tb
+        assert k == 0 or not (sa + (k - 1) * ta < sb + (k - 1) * tb)

@@ -3,7 +3,8 @@ mathematics, never against the oracle itself.
 
 * dense triangular solves (scipy/LAPACK) on tiny random patterns
 * manufactured solutions (x chosen, b = A x through scipy)
-* closed forms for levels (Sec. 4.1: nlev = nx+ny-1 and nx+ny+nz-2)
+* closed forms for levels (Sec. 4.1: nlev = nx+ny-1 and nx+ny+nz-2; derived
+  here for the 9- and 27-point stencils of Sec. 5.1)
 * the worked example of Fig. 1 (golden fixture)
 * brute-force longest paths on tiny random DAGs
 * level invariants (one level per row, deps strictly lower, tightness)
@@ -160,6 +161,49 @@ def test_levels_closed_form_3d(dims):
     levu, nlevu = oracle.levels(U.rowptr, U.colidx, upper=True)
     assert nlevu == nx + ny + nz - 2
     assert np.array_equal(levu, (nx - 1 - x) + (ny - 1 - y) + (nz - 1 - z))
+
+
+@pytest.mark.parametrize("nx,ny", [(2, 2), (7, 5), (5, 9), (64, 16)])
+def test_levels_closed_form_9pt(nx, ny):
+    """9-point stencil (Sec. 5.1, Table 2), nx >= 2: the dependency on
+    (x+1, y-1) makes each grid line two levels deep, so lev = x + 2y and
+    nlev = nx + 2 ny - 2 (the upper sweep is the point reflection)."""
+    L, U = synth.laplacian_triangles((nx, ny), 9)
+    x, y = np.arange(L.n) % nx, np.arange(L.n) // nx
+    lev, nlev = oracle.levels(L.rowptr, L.colidx)
+    assert nlev == nx + 2 * ny - 2
+    assert np.array_equal(lev, x + 2 * y)
+    levu, nlevu = oracle.levels(U.rowptr, U.colidx, upper=True)
+    assert nlevu == nlev
+    assert np.array_equal(levu, (nx - 1 - x) + 2 * (ny - 1 - y))
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2), (6, 5, 4), (4, 7, 9)])
+def test_levels_closed_form_27pt(dims):
+    """27-point stencil, nx, ny >= 2: the dependencies on (x+1, y-1, z) and
+    (x+1, y+1, z-1) give lev = x + 2y + 4z, nlev = nx + 2 ny + 4 nz - 6."""
+    nx, ny, nz = dims
+    L, U = synth.laplacian_triangles(dims, 27)
+    i = np.arange(L.n)
+    x, y, z = i % nx, (i // nx) % ny, i // (nx * ny)
+    lev, nlev = oracle.levels(L.rowptr, L.colidx)
+    assert nlev == nx + 2 * ny + 4 * nz - 6
+    assert np.array_equal(lev, x + 2 * y + 4 * z)
+    levu, nlevu = oracle.levels(U.rowptr, U.colidx, upper=True)
+    assert nlevu == nlev
+    assert np.array_equal(levu, (nx - 1 - x) + 2 * (ny - 1 - y) + 4 * (nz - 1 - z))
+
+
+def test_levels_closed_form_table2_grids():
+    """Level counts of the Table 2 grids follow the closed forms (and grow
+    with the aspect ratios of eq. (5), as Sec. 5.1 says)."""
+    for nx, ny in synth.TABLE2_GRIDS_2D[:2]:
+        for pts, want in ((5, nx + ny - 1), (9, nx + 2 * ny - 2)):
+            L, _ = synth.laplacian_triangles((nx, ny), pts)
+            assert oracle.levels(L.rowptr, L.colidx)[1] == want
+    nx, ny, nz = synth.TABLE2_GRIDS_3D[-1]
+    L, _ = synth.laplacian_triangles((nx, ny, nz), 7)
+    assert oracle.levels(L.rowptr, L.colidx)[1] == nx + ny + nz - 2
 
 
 def read_golden_fig1():

@@ -37,6 +37,41 @@ def laplacian_7pt_dense(nx, ny, nz):
     return A
 
 
+def king_laplacian_dense(dims):
+    """Graph Laplacian of the grid in which every point is joined to every
+    point at Chebyshev distance 1 (the 9-point and 27-point stencils),
+    built point by point."""
+    n = int(np.prod(dims))
+    A = np.zeros((n, n))
+    coords = list(np.ndindex(*dims[::-1]))
+    index = {c[::-1]: k for k, c in enumerate(coords)}
+    for p, i in index.items():
+        for q, j in index.items():
+            if i != j and max(abs(a - b) for a, b in zip(p, q)) == 1:
+                A[i, j] = -1.0
+    np.fill_diagonal(A, 3 ** len(dims) - 1)
+    return A
+
+
+@pytest.mark.parametrize("dims,pts", [((4, 3), 9), ((3, 4, 2), 27), ((5, 4), 5),
+                                      ((3, 3, 4), 7)])
+def test_laplacian_triangles(dims, pts):
+    L, U = synth.laplacian_triangles(dims, pts)
+    check_csr(L)
+    check_csr(U)
+    Ld, Ud = L.scipy().toarray(), U.scipy().toarray()
+    assert np.array_equal(np.triu(Ld, 1), 0 * Ld) and np.array_equal(np.tril(Ud, -1), 0 * Ud)
+    np.testing.assert_array_equal(np.diag(Ld), np.diag(Ud))
+    A = Ld + Ud - np.diag(np.diag(Ld))
+    if pts in (9, 27):
+        np.testing.assert_array_equal(A, king_laplacian_dense(dims))
+    else:
+        # 5/7 points: the axis neighbours only, diagonal 2 * dimensions
+        assert np.all(np.diag(A) == 2 * len(dims))
+        assert np.count_nonzero(A - np.diag(np.diag(A))) == 2 * (L.nnz - L.n)
+    assert L.meta["points"] == pts and not L.upper and U.upper
+
+
 def test_ilu0_factors_match_generic_ilu0():
     nx, ny, nz = 6, 5, 4
     Lw, Uw = generic_ilu0(laplacian_7pt_dense(nx, ny, nz))
