@@ -200,7 +200,9 @@ def main():
                          "--lanes/--max-blocks/--algo and run --repeat solves, nothing else")
     ap.add_argument("--lanes", type=int, default=4)
     ap.add_argument("--max-blocks", type=int, default=304)
-    ap.add_argument("--algo", default="self", choices=["self", "level", "tiled", "chains"])
+    ap.add_argument("--algo", default="self",
+                    choices=["self", "level", "tiled", "chains", "permuted", "column"])
+    ap.add_argument("--block", type=int, default=256)
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--extended", action="store_true",
                     help="also measure the general, multi-RHS, batched, refined and autograd "
@@ -430,7 +432,7 @@ def single_solve(args):
         A, bh = (L, bL) if args.single_solve == "L" else (U, bU)
     p = TriangularPlan(torch.tensor(A.rowptr, device=dev), torch.tensor(A.colidx, device=dev),
                        torch.tensor(A.vals, device=dev), upper=A.upper, unit=A.unit)
-    p.set_tuning(args.lanes, 256, args.max_blocks)
+    p.set_tuning(args.lanes, args.block, args.max_blocks)
     b = torch.tensor(bh, device=dev)
     x = torch.empty_like(b)
     for _ in range(args.repeat):
@@ -438,7 +440,8 @@ def single_solve(args):
     torch.cuda.synchronize()
     err = float(np.max(np.abs(x.cpu().numpy() - xt)) / np.max(np.abs(xt)))
     print(json.dumps({"single_solve": args.single_solve, "algo": args.algo, "lanes": args.lanes,
-                      "max_blocks": args.max_blocks, "max_rel_err_vs_xtrue": err}))
+                      "block": args.block, "max_blocks": args.max_blocks,
+                      "max_rel_err_vs_xtrue": err}))
 
 
 def table2_sweep(args):
@@ -471,8 +474,8 @@ def table2_sweep(args):
             pl, pu = dplan(L), dplan(U)
             b = torch.tensor(bh, device=dev, dtype=dtype)
             y, x = torch.empty_like(b), torch.empty_like(b)
-            kw = dict(algos=("self", "permuted"), lanes=(1, 2, 4, 8, 16), blocks=(256, 512),
-                      grids=(0, 2), reps=3)
+            kw = dict(algos=("self", "permuted", "tiled"), lanes=(1, 2, 4, 8, 16),
+                      blocks=(256, 512), grids=(0, 2), tiles=(1024, 4096), reps=3)
             tl = autotune.tune_algos(pl, b, y, **kw)
             pl.solve(b, out=y, algo="auto")
             tu = autotune.tune_algos(pu, y, x, **kw)
@@ -486,11 +489,9 @@ def table2_sweep(args):
             lv_ms = _events_ms(lambda: pair("level"), 2)
             esz = 8 if dtype == torch.float64 else 4
             byts = effective_bytes(L.n, L.nnz, esz) + effective_bytes(U.n, U.nnz, esz)
-            cus = None
-            if dtype == torch.float64:
-                cl = cusparse_single(L, pl, b, dev)
-                cu = cusparse_single(U, pu, y, dev)
-                cus = cl + cu if cl is not None and cu is not None else None
+            cl = cusparse_single(L, pl, b, dev)
+            cu = cusparse_single(U, pu, y, dev)
+            cus = cl + cu if cl is not None and cu is not None else None
             row = {"grid": "x".join(map(str, dims)), "points": pts, "dtype": dname,
                    "n": L.n, "nnz_A": nnz_a,
                    "aspect": dims[1] // dims[0] if len(dims) == 2 else dims[2] // dims[0],

@@ -213,15 +213,17 @@ sptrsv_status_t kahn_levels(sptrsv_plan_t P, const int* ptr, const int* idx, con
     int* scratch = nullptr;
     // Layout (ints): [0, 2) the 64-bit barrier counter, which must be 8-byte
     // aligned and so comes first (cudaMalloc returns 256-byte aligned
-    // memory); [2] queue end; [3] level count; then count0, count, queue.
-    CK(cudaMalloc(&scratch, sizeof(int) * (3 * (size_t)n + 4)));
+    // memory); [2, 6) the queue end / rotating level counters (the roots are
+    // counted in [2]; [5] = rows leveled by the persistent form); [6] level
+    // count; [7] pad; then count0, count, queue.
+    CK(cudaMalloc(&scratch, sizeof(int) * (3 * (size_t)n + 8)));
     unsigned long long* arrivals = (unsigned long long*)scratch;
     int* qend = scratch + 2;
-    int* nlev_dev = scratch + 3;
-    int* count0 = scratch + 4;
+    int* nlev_dev = scratch + 6;
+    int* count0 = scratch + 8;
     int* count = count0 + n;
     int* queue = count + n;
-    cudaError_t e = cudaMemsetAsync(scratch, 0, 4 * sizeof(int), s);
+    cudaError_t e = cudaMemsetAsync(scratch, 0, 8 * sizeof(int), s);
     if (e == cudaSuccess) e = launch_column_counts(n, ptr, idx, count0, s);
     if (e == cudaSuccess) e = launch_kahn_roots(n, count0, count, L.lev, queue, qend, s);
     int h_last = 0, level = 0;
@@ -233,7 +235,7 @@ sptrsv_status_t kahn_levels(sptrsv_plan_t P, const int* ptr, const int* idx, con
                                    P->status, P->spin.limit, (int)grid, block, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&level, nlev_dev, sizeof(int),
                                                   cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&h_last, qend, sizeof(int),
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&h_last, qend + 3, sizeof(int),
                                                   cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     } else if (e == cudaSuccess) {

@@ -151,8 +151,10 @@ cudaError_t launch_kahn_level(const int* dptr, const int* didx, int* count, int*
                               int* qend, int n, int first, int last, int level,
                               unsigned long long* status, int max_grid, cudaStream_t s);
 int kahn_persistent_blocks_per_sm(int block);
+// cnt[0] = roots queued by launch_kahn_roots, cnt[1] = cnt[2] = 0; on exit
+// cnt[3] = rows leveled and *nlev_out = levels.
 cudaError_t launch_kahn_persistent(const int* dptr, const int* didx, int* count, int* lev,
-                                   int* queue, int* qend, int n, unsigned long long* arrivals,
+                                   int* queue, int* cnt, int n, unsigned long long* arrivals,
                                    int* nlev_out, unsigned long long* status, long long limit,
                                    int grid, int block, cudaStream_t s);
 

@@ -127,37 +127,59 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* arrivals,
     return s_ok != 0;
 }
 
-// Persistent driver: the frontier of level L is queue[first, last); its
-// removal appends the roots of level L + 1 at *qend, so after the barrier
-// the next frontier is queue[last, *qend).  Stops when a level exposes no
-// new root and writes the number of levels.
+// Persistent driver.  The frontier of level L is queue[base_L, base_L +
+// size_L); its removal appends the roots of level L + 1 right after it.
+// Level sizes live in three rotating counters cnt[L % 3]: the value a block
+// reads after a barrier must not move while slower blocks still read it, so
+// the roots of level L + 1 are counted in cnt[(L+1) % 3] (not in the one
+// being read), and block 0 clears cnt[(L+2) % 3] during level L: every block
+// read that counter (size of level L - 1) before arriving at the barrier
+// that opened level L, and nobody appends to it before the next barrier.
+// cnt[0] holds the roots queued by kahn_roots_k; cnt[1] and cnt[2] start at
+// zero.  Stops when a level exposes no new root and writes the level count.
 __global__ void kahn_persistent_k(const int* __restrict__ dptr, const int* __restrict__ didx,
-                                  int* count, int* lev, int* queue, int* qend, int n,
+                                  int* count, int* lev, int* queue, int* cnt, int n,
                                   unsigned long long* arrivals, int* nlev_out,
                                   unsigned long long* status, long long limit) {
     const int lane = threadIdx.x & 31;
     const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
     const long long wid = (((long long)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5);
     unsigned long long gen = 0;
-    // the roots were queued by kahn_roots_k before this launch
-    int first = 0;
-    int last = *(volatile int*)qend;
+    long long base = 0;
+    int size = *(volatile int*)cnt;  // roots, queued before this launch
     int level = 0;
-    while (last > first) {
+    while (size > 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) cnt[(level + 2) % 3] = 0;
+        int* tail = cnt + (level + 1) % 3;
+        int* next = queue + base + size;  // where the roots of level + 1 go
         // queue entries of this frontier were written by other SMs during the
         // previous level: read them from L2 (__ldcg), never from a stale L1 line
-        for (long long w = wid; first + w < last; w += warps)
-            kahn_remove(dptr, didx, count, lev, queue, qend, n, __ldcg(queue + first + w), level,
-                        lane, status);
+        for (long long w = wid; w < size; w += warps) {
+            const int i = __ldcg(queue + base + w);
+            const int beg = dptr[i], end = dptr[i + 1];
+            for (int q = beg + lane; q < end; q += 32) {
+                const int r = didx[q];
+                if (r == i) continue;
+                if (atomicSub(count + r, 1) == 1) {
+                    lev[r] = level + 1;
+                    const int at = atomicAdd(tail, 1);
+                    if (base + size + at < n) next[at] = r;
+                    else report(status, r, kCodeInternal);
+                }
+            }
+        }
         ++gen;
         if (!grid_barrier(arrivals, gen * gridDim.x, limit, status, level)) return;
-        int nl;
-        asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(nl) : "l"(qend) : "memory");
-        first = last;
-        last = nl;
+        int nsz;
+        asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(nsz) : "l"(tail) : "memory");
+        base += size;
+        size = nsz;
         ++level;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) *nlev_out = level;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *nlev_out = level;
+        cnt[3] = (int)base;  // rows leveled, checked by the host
+    }
 }
 
 int kahn_persistent_blocks_per_sm(int block) {
@@ -170,11 +192,11 @@ int kahn_persistent_blocks_per_sm(int block) {
 }
 
 cudaError_t launch_kahn_persistent(const int* dptr, const int* didx, int* count, int* lev,
-                                   int* queue, int* qend, int n, unsigned long long* arrivals,
+                                   int* queue, int* cnt, int n, unsigned long long* arrivals,
                                    int* nlev_out, unsigned long long* status, long long limit,
                                    int grid, int block, cudaStream_t s) {
     void* args[] = {(void*)&dptr, (void*)&didx, (void*)&count,    (void*)&lev,
-                    (void*)&queue, (void*)&qend, (void*)&n,        (void*)&arrivals,
+                    (void*)&queue, (void*)&cnt,  (void*)&n,        (void*)&arrivals,
                     (void*)&nlev_out, (void*)&status, (void*)&limit};
     return cudaLaunchCooperativeKernel((const void*)kahn_persistent_k, dim3(grid), dim3(block),
                                        args, 0, s);
