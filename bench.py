@@ -211,6 +211,10 @@ def main():
                     help="instead of the headline line, print the Table 2 sweep: the solve "
                          "pair of eq. (3) on the 5/9-point 2-D and 7/27-point 3-D Laplacians "
                          "of every Table 2 grid, FP64 and FP32 (minutes)")
+    ap.add_argument("--tune-cache", default=None,
+                    help="JSON file of autotuner choices: applied if it exists, written "
+                         "after tuning otherwise (lets a profiler run reuse the plain run's "
+                         "choices instead of re-tuning under the profiler)")
     ap.add_argument("--sweep-grids", type=int, default=5,
                     help="grids per stencil in --sweep (the first k of Table 2)")
     args = ap.parse_args()
@@ -247,11 +251,26 @@ def main():
                               torch.tensor(A.vals, device=dev), upper=A.upper, unit=A.unit)
 
     pl, pu = dplan(L), dplan(U)
+    setup = {"L": pl.analysis_ms, "U": pu.analysis_ms,
+             "method": [pl.analysis_method(), pu.analysis_method()],
+             "note": "plan creation: validation, transposed pattern, levels "
+                     "(SPTRSV_ANALYSIS_AUTO), level sets"}
     b = torch.tensor(b_host, device=dev)
     y = torch.empty_like(b)
     x = torch.empty_like(b)
-    tune_l = autotune.tune_algos(pl, b, y, reps=5)
-    tune_u = autotune.tune_algos(pu, y, x, reps=5)
+    cached = None
+    if args.tune_cache and os.path.exists(args.tune_cache):
+        with open(args.tune_cache) as f:
+            cached = json.load(f)
+    if cached:
+        tune_l = autotune.apply_choice(pl, cached["L"])
+        tune_u = autotune.apply_choice(pu, cached["U"])
+    else:
+        tune_l = autotune.tune_algos(pl, b, y, reps=5)
+        tune_u = autotune.tune_algos(pu, y, x, reps=5)
+        if args.tune_cache:
+            with open(args.tune_cache, "w") as f:
+                json.dump({"L": autotune.choice(tune_l), "U": autotune.choice(tune_u)}, f)
 
     def step(algo="auto"):
         pl.solve(b, out=y, algo=algo)
@@ -313,9 +332,48 @@ def main():
     for _ in range(e2e_steps):
         e2e_step()
     torch.cuda.synchronize()
+    e2e_serial_s = time.perf_counter() - t0
+    e2e_serial_err = float(np.max(np.abs(hx.numpy() - xt)) / np.max(np.abs(xt)))
+
+    # The same steps pipelined the way a caller streaming right-hand sides
+    # would run them: each step's H2D copy, its two solves and its D2H copy
+    # are ordered by events on three streams (double-buffered device vectors),
+    # so the copies of neighbouring steps overlap the latency-bound solves.
+    s_in, s_cmp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    dbs = [torch.empty_like(b) for _ in range(2)]
+    dxs = [torch.empty_like(b) for _ in range(2)]
+    hxs = [torch.empty_like(hb).pin_memory() for _ in range(2)]
+    ev = {k: [torch.cuda.Event() for _ in range(2)] for k in ("in", "used", "out", "read")}
+
+    def e2e_pipelined(steps):
+        for k in range(steps):
+            j = k % 2
+            if k >= 2:
+                s_in.wait_event(ev["used"][j])
+            with torch.cuda.stream(s_in):
+                dbs[j].copy_(hb, non_blocking=True)
+            ev["in"][j].record(s_in)
+            s_cmp.wait_event(ev["in"][j])
+            if k >= 2:
+                s_cmp.wait_event(ev["read"][j])
+            pl.solve(dbs[j], out=dy, algo="auto", stream=s_cmp)
+            ev["used"][j].record(s_cmp)
+            pu.solve(dy, out=dxs[j], algo="auto", stream=s_cmp)
+            ev["out"][j].record(s_cmp)
+            s_out.wait_event(ev["out"][j])
+            with torch.cuda.stream(s_out):
+                hxs[j].copy_(dxs[j], non_blocking=True)
+            ev["read"][j].record(s_out)
+
+    torch.cuda.synchronize()
+    e2e_pipelined(3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_pipelined(e2e_steps)
+    torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e_value = 2 * e2e_steps * world / e2e_s
-    e2e_err = float(np.max(np.abs(hx.numpy() - xt)) / np.max(np.abs(xt)))
+    e2e_err = max(float(np.max(np.abs(h.numpy() - xt)) / np.max(np.abs(xt))) for h in hxs)
 
     extra = {}
     if not args.no_compare:
@@ -343,13 +401,36 @@ def main():
                                     "graph_solves_per_s": 2e3 / lvg_ms}
         extra["cusparse_spsv"] = cusparse_pair(L, U, pl, pu, b, dev, lv_steps)
         self_ms = ms / args.steps
+        # dependency-latency bound: a bidiagonal chain (n = 10^5, every row
+        # waits on the previous one) gives the time of one dependency hop
+        # t_hop; a solve of nlev levels cannot beat nlev * t_hop
+        extra["latency_bound"] = chain_latency(dev, [pl.levels()["nlev"], pu.levels()["nlev"]],
+                                               kernel_avg_ms)
         # setup phase (Sec. 4.4): the sync-free sweep against Kahn's algorithm
         # (Sec. 4.4.1), as the paper runs it (host loop) and in one persistent
         # launch; every method yields the same levels
+        # the column-wise self-scheduled solve (Alg. 4, SLFC), the paper's
+        # fastest on P100, tuned on its own and timed on the same pair
+        kw = dict(lanes=(1, 2, 4, 8), blocks=(128, 256), grids=(0, 4, 2), reps=3)
+        col_l = autotune.tune(pl, b, y, algo="column", **kw)
+        col_u = autotune.tune(pu, y, x, algo="column", **kw)
+
+        def col_step():
+            pl.solve(b, out=y, algo="column")
+            pu.solve(y, out=x, algo="column")
+
+        col_ms = _events_ms(col_step, lv_steps)
+        col_err = float(np.max(np.abs(x.cpu().numpy() - xt)) / np.max(np.abs(xt)))
+        extra["column_wise_slfc"] = {"ms_per_step": col_ms, "solves_per_s": 2e3 / col_ms,
+                                     "lanes": [col_l["best"][0], col_u["best"][0]],
+                                     "row_wise_speedup": col_ms / self_ms,
+                                     "max_rel_err_vs_xtrue": col_err}
+        autotune.apply_choice(pl, autotune.choice(tune_l))
+        autotune.apply_choice(pu, autotune.choice(tune_u))
         methods = {}
-        for m in ("sweep", "kahn_host_loop", "kahn_persistent"):
+        for m in ("sweep", "kahn_host_loop", "kahn_persistent", "auto"):
             methods[m] = [pl.reanalyze(m), pu.reanalyze(m)]
-        best_setup = min(sum(v) for v in methods.values())
+        best_setup = sum(methods["auto"])
         extra["analysis_methods_ms"] = {"L_U": methods, "fields": "[L, U] wall ms, level "
                                         "analysis + level sets (+ transposed pattern for Kahn)"}
         cus = extra["cusparse_spsv"]
@@ -392,6 +473,8 @@ def main():
                        "l2": "inputs larger than L2 (2 x 150 MB of matrix+vectors per step)",
                        "parallelism": f"replicas x{world}"},
             "effective_gbs": value * bytes_solve / 1e9,
+            # eq. (4): 2 nnz(A) / t for the pair, A = L + U - I (the 7-point operator)
+            "gflops_eq4": 2 * (L.nnz + U.nnz - n) / (ms / args.steps / 1e3) / 1e9,
             "bytes_per_solve": bytes_solve,
             "roofline": {"bound": "hbm",
                          "kernel": KERNELS[tune_l["algo"]][0],
@@ -402,10 +485,15 @@ def main():
                          "kernel_source_sha": sha},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": n * 8,
-                    "d2h_bytes_per_step": n * 8, "steps": e2e_steps, "max_rel_err": e2e_err},
+                    "d2h_bytes_per_step": n * 8, "steps": e2e_steps, "max_rel_err": e2e_err,
+                    "how": "public API, pinned host b -> device -> L solve -> U solve -> host "
+                           "x every step; copies and solves on three streams ordered by "
+                           "events, double-buffered (host wall clock)",
+                    "serial_value": 2 * e2e_steps * world / e2e_serial_s,
+                    "serial_max_rel_err": e2e_serial_err},
             "gpu_launches": launches,
             "clocks": clk.summary(),
-            "analysis_ms": {"L": pl.analysis_ms, "U": pu.analysis_ms},
+            "analysis_ms": setup,
             "max_rel_err_vs_xtrue": err,
         }
         line.update(extra)
@@ -492,6 +580,10 @@ def table2_sweep(args):
             cl = cusparse_single(L, pl, b, dev)
             cu = cusparse_single(U, pu, y, dev)
             cus = cl + cu if cl is not None and cu is not None else None
+            analysis = None
+            if dtype == torch.float64:
+                analysis = {m: pl.reanalyze(m) for m in ("sweep", "kahn_persistent", "auto")}
+                analysis["auto_picks"] = pl.analysis_method()
             row = {"grid": "x".join(map(str, dims)), "points": pts, "dtype": dname,
                    "n": L.n, "nnz_A": nnz_a,
                    "aspect": dims[1] // dims[0] if len(dims) == 2 else dims[2] // dims[0],
@@ -502,6 +594,7 @@ def table2_sweep(args):
                    "level_ms": lv_ms, "speedup_vs_level": lv_ms / ms,
                    "cusparse_ms": cus, "speedup_vs_cusparse": (cus / ms) if cus else None,
                    "lanes": [tl["best"][0], tu["best"][0]], "algo": [tl["algo"], tu["algo"]],
+                   "analysis_ms_L": analysis,
                    "max_rel_err_vs_xtrue": err}
             rows.append(row)
             print(json.dumps(row), file=sys.stderr, flush=True)
@@ -509,6 +602,39 @@ def table2_sweep(args):
             pu.close()
     print(json.dumps({"sweep": "table2", "unit_note": "ms per solve pair (L then U)",
                       "rows": rows}), flush=True)
+
+
+def chain_latency(dev, nlevs, kernel_avg_ms, n=100_000):
+    """Time of one dependency hop of the self-scheduled solve, from a lower
+    bidiagonal chain of n rows (nlev = n): with one row per warp (32 lanes)
+    every hop is a handshake between warps through L2; with 32 rows per warp
+    (1 lane) consecutive rows share a warp.  Returns the hop times and the
+    bound nlev * t_hop for the given level counts."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1710_04985_gb300 import TriangularPlan
+    rows = np.repeat(np.arange(n), 2)[1:]
+    cols = np.concatenate(([0], np.stack([np.arange(n - 1), np.arange(1, n)], 1).ravel()))
+    vals = np.where(rows == cols, 2.0, -1.0)
+    A = synth._from_sorted_coo(n, rows, cols, vals, upper=False)
+    p = TriangularPlan(torch.tensor(A.rowptr, device=dev), torch.tensor(A.colidx, device=dev),
+                       torch.tensor(A.vals, device=dev))
+    b = torch.ones(n, dtype=torch.float64, device=dev)
+    x = torch.empty_like(b)
+    hops = {}
+    for lanes in (32, 1):
+        p.set_tuning(lanes, 256, 0)
+        hops[f"lanes{lanes}"] = _events_ms(lambda: p.solve(b, out=x, algo="self"), 3) * 1e3 / n
+    p.close()
+    t_hop = hops["lanes32"]
+    bound_ms = [nl * t_hop / 1e3 for nl in nlevs]
+    return {"t_hop_us": hops, "nlev": nlevs, "bound_ms_per_solve": bound_ms,
+            "kernel_avg_ms": kernel_avg_ms,
+            "frac_of_bound": (sum(bound_ms) / len(bound_ms)) / kernel_avg_ms,
+            "how": "lower bidiagonal chain n = 1e5, FP64, self-scheduled in place; "
+                   "t_hop with one row per warp; frac = bound / measured kernel time"}
 
 
 def _break_even(setup_a, solve_a, setup_b, solve_b):
@@ -578,6 +704,17 @@ def extended(dev, args):
                      "max_rel_err_vs_oracle": err}
         if dtype == torch.float64:
             gen[name]["cusparse_ms"] = cusparse_single(A, p, b, dev)
+            ch = autotune.choice(t)
+            tc = autotune.tune(p, b, x, algo="column", lanes=(8, 16, 32), blocks=(256,),
+                               grids=(0, 2), reps=2)
+            gen[name]["column_wise_slfc_ms"] = _events_ms(
+                lambda: p.solve(b, out=x, algo="column"), 3)
+            gen[name]["column_wise_lanes"] = tc["best"][0]
+            autotune.apply_choice(p, ch)
+            gen[name]["analysis_methods_ms"] = {
+                m: p.reanalyze(m) for m in ("sweep", "kahn_host_loop", "kahn_persistent",
+                                            "auto")}
+            gen[name]["analysis_auto_picks"] = p.analysis_method()
         p.close()
     res["general_1M"] = gen
 

@@ -129,7 +129,18 @@ typedef enum {
                                      lower/upper matrix): allocates, synchronises the
                                      stream, refused with SPTRSV_ERR_NOT_SUPPORTED
                                      during graph capture.  One right-hand side; more
-                                     columns fall back to SPTRSV_ALGO_SELF               */
+                                     columns fall back to SPTRSV_ALGO_SELF               */,
+    SPTRSV_ALGO_SELF_BLOCKED = 6  /* Alg. 3 on the level-ordered copy (as
+                                     SPTRSV_ALGO_SELF_PERMUTED, same first-use build
+                                     and value snapshot), a thread block per tile of
+                                     tile_rows consecutive level-order positions
+                                     (sptrsv_set_tiling; level_order is ignored):
+                                     dependencies inside the tile pass through shared
+                                     memory, warps take row groups dynamically, the
+                                     tile's rows are prefetched into L2.  For narrow
+                                     levels.  Bitwise equal to SPTRSV_ALGO_SELF for
+                                     equal lanes.  One right-hand side; more columns
+                                     fall back to SPTRSV_ALGO_SELF                       */
 } sptrsv_algo_t;
 
 /* Level-analysis methods (sptrsv_reanalyze).  All give the same levels and
@@ -141,18 +152,25 @@ typedef enum {
     SPTRSV_ANALYSIS_KAHN_HOST_LOOP = 1,   /* Kahn's algorithm as in Sec. 4.4.1: one
                                              launch and one device-to-host copy per
                                              level                                  */
-    SPTRSV_ANALYSIS_KAHN_PERSISTENT = 2   /* Kahn's algorithm in one cooperative
+    SPTRSV_ANALYSIS_KAHN_PERSISTENT = 2,  /* Kahn's algorithm in one cooperative
                                              launch, levels separated by a bounded
                                              grid-wide barrier                      */
+    SPTRSV_ANALYSIS_AUTO = 3              /* what sptrsv_analyze does: the persistent
+                                             Kahn launch, which gives up after 256
+                                             levels if they hold fewer than 112 rows
+                                             on average (a deep, narrow graph), and
+                                             then the sweep                         */
 } sptrsv_analysis_t;
 
 /* ------------------------------------------------------------------ setup */
 
-/* Setup phase (Sec. 4.4, Table 1): validates the CSR (Sec. 3), computes the
- * 0-based level of every row, lev(i) = 1 + max lev(j) over the off-diagonal
- * entries j of row i (Sec. 4.1; roots get 0), and the level sets
- * (nlev, ilev[nlev+1], jlev[n]) with rows in ascending index order inside a
- * level.  An upper triangle is swept in reverse (Sec. 4.1).
+/* Setup phase (Sec. 4.4, Table 1): validates the CSR (Sec. 3), builds the
+ * CSR of the transpose (pattern and value map, Table 1's TRANS_GPU), computes
+ * the 0-based level of every row, lev(i) = 1 + max lev(j) over the
+ * off-diagonal entries j of row i (Sec. 4.1; roots get 0) with
+ * SPTRSV_ANALYSIS_AUTO, and the level sets (nlev, ilev[nlev+1], jlev[n])
+ * with rows in ascending index order inside a level.  An upper triangle is
+ * swept in reverse (Sec. 4.1).
  *   n, nnz        matrix order and stored entries (0 <= n, 0 <= nnz < 2^31)
  *   d_rowptr ...  device CSR, borrowed until sptrsv_free (see above)
  *   dtype         element type of d_vals
@@ -178,6 +196,12 @@ SPTRSV_API sptrsv_status_t sptrsv_analyze(int n, int nnz, const int *d_rowptr,
  * SPTRSV_ERR_NOT_SUPPORTED during graph capture. */
 SPTRSV_API sptrsv_status_t sptrsv_reanalyze(sptrsv_plan_t plan, int transpose,
                                             sptrsv_analysis_t method, void *stream);
+
+/* The analysis method that produced the forward (transpose = 0) or
+ * transposed (transpose = 1) levels: SWEEP, KAHN_HOST_LOOP or
+ * KAHN_PERSISTENT (AUTO resolves to one of them). */
+SPTRSV_API sptrsv_status_t sptrsv_analysis_method(sptrsv_plan_t plan, int transpose,
+                                                  int *method);
 
 /* Releases everything the plan owns (synchronises the device first). */
 SPTRSV_API sptrsv_status_t sptrsv_free(sptrsv_plan_t plan);

@@ -21,12 +21,12 @@ ERR_TIMEOUT = 6
 ERR_NOT_SUPPORTED = 7
 ERR_INTERNAL = 8
 
-ANALYSIS_SWEEP, ANALYSIS_KAHN_HOST_LOOP, ANALYSIS_KAHN_PERSISTENT = 0, 1, 2
+ANALYSIS_SWEEP, ANALYSIS_KAHN_HOST_LOOP, ANALYSIS_KAHN_PERSISTENT, ANALYSIS_AUTO = 0, 1, 2, 3
 F64, F32 = 0, 1
 LOWER, UPPER = 0, 1
 NON_UNIT, UNIT = 0, 1
 (ALGO_LEVEL, ALGO_SELF, ALGO_SELF_TILED, ALGO_SELF_CHAINS, ALGO_SELF_PERMUTED,
- ALGO_SELF_COLUMN) = 0, 1, 2, 3, 4, 5
+ ALGO_SELF_COLUMN, ALGO_SELF_BLOCKED) = 0, 1, 2, 3, 4, 5, 6
 
 # (name, restype, argtypes) for every entry point of include/sptrsv.h
 _c_int, _c_ll, _c_dbl = ctypes.c_int, ctypes.c_longlong, ctypes.c_double
@@ -37,6 +37,7 @@ SIGNATURES = [
     ("sptrsv_analyze", _c_int, [_c_int, _c_int, _vp, _vp, _vp, _c_int, _c_int, _c_int, _vp, _pp]),
     ("sptrsv_free", _c_int, [_vp]),
     ("sptrsv_reanalyze", _c_int, [_vp, _c_int, _c_int, _vp]),
+    ("sptrsv_analysis_method", _c_int, [_vp, _c_int, _ip]),
     ("sptrsv_solve", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _c_int, _vp]),
     ("sptrsv_solve_transpose", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _c_int, _vp]),
     ("sptrsv_prepare_transpose", _c_int, [_vp, _vp]),

@@ -6,9 +6,9 @@ sub-warp width (lanes per row, hence rows per warp = 32 / lanes) at the
 default block size, then, for that width, the block size and the cap on the
 persistent grid (how many warps wait ahead of the dependency frontier: more
 hides latency, fewer polls less L2 traffic), and for the tiled form the tile
-size.  ``tune_algos`` runs ``tune`` for the level-ordered (in place and on
-the level-ordered copy), tiled and chained self-scheduled forms and keeps the
-fastest, recording it on the plan.
+size.  ``tune_algos`` runs ``tune`` for the level-ordered (in place, on the
+level-ordered copy, and blocked on that copy), tiled and chained
+self-scheduled forms and keeps the fastest, recording it on the plan.
 Results are cached per matrix signature for the process.
 """
 from __future__ import annotations
@@ -67,9 +67,11 @@ def tune(plan, b, x=None, algo="self", lanes=LANES, blocks=BLOCKS, grids=GRID_FR
     esize = 8 if plan.dtype == torch.float64 else 4
     table = []
 
+    tiles_used = algo in ("tiled", "blocked")
+
     def run(w, blk, mb, tile, order):
         plan.set_tuning(w, blk, mb)
-        if algo == "tiled":
+        if tiles_used:
             plan.set_tiling(tile, order)
         ms = time_solve(plan, b, x, algo, reps, transpose)
         table.append((w, blk, mb, ms, tile, order))
@@ -77,18 +79,18 @@ def tune(plan, b, x=None, algo="self", lanes=LANES, blocks=BLOCKS, grids=GRID_FR
 
     default_block = 256 if 256 in blocks else blocks[0]
     tile0 = 2048 if 2048 in tiles else tiles[0]
-    first_grid = 2 * sms if algo == "tiled" else 0
+    first_grid = 2 * sms if tiles_used else 0
     orders = tile_orders if algo == "tiled" else (False,)
     for order in orders:
         for w in lanes:
             run(w, default_block, first_grid, tile0, order)
     w_best, order_best = min(table, key=lambda r: r[3])[0], min(table, key=lambda r: r[3])[5]
-    if algo in ("self", "tiled", "chains", "permuted"):
+    if algo in ("self", "tiled", "chains", "permuted", "blocked"):
         for blk in blocks:
             for frac in grids:
                 if (blk, frac * sms) != (default_block, first_grid):
                     run(w_best, blk, frac * sms, tile0, order_best)
-    if algo == "tiled":
+    if tiles_used:
         bb = min(table, key=lambda r: r[3])
         for tile in tiles:
             if tile != tile0 and tile * esize <= 48 * 1024 - 256:
@@ -102,11 +104,11 @@ def tune(plan, b, x=None, algo="self", lanes=LANES, blocks=BLOCKS, grids=GRID_FR
 
 def _apply(plan, best, algo):
     plan.set_tuning(best[0], best[1], best[2])
-    if algo == "tiled":
+    if algo in ("tiled", "blocked"):
         plan.set_tiling(best[4], best[5])
 
 
-def tune_algos(plan, b, x=None, algos=("self", "permuted", "tiled", "chains"), reps=3,
+def tune_algos(plan, b, x=None, algos=("self", "permuted", "blocked", "tiled", "chains"), reps=3,
                use_cache=True, **kw):
     """Tune each self-scheduled form and keep the faster one.
 
@@ -114,16 +116,40 @@ def tune_algos(plan, b, x=None, algos=("self", "permuted", "tiled", "chains"), r
     sets ``plan.best_algo`` (used by ``plan.solve(..., algo="auto")``)."""
     nrhs = 1 if b.dim() == 1 else b.shape[1]
     if nrhs > 1:
-        algos = tuple(a for a in algos if a not in ("tiled", "chains", "permuted")) or ("self",)
+        algos = tuple(a for a in algos
+                      if a not in ("tiled", "chains", "permuted", "blocked")) or ("self",)
     per = {}
     for a in algos:
         if a == "tiled" and not kw:
             # a lighter search: the tiled form wins only on chain-like matrices
             per[a] = tune(plan, b, x, algo=a, reps=reps, use_cache=use_cache, lanes=(1, 4, 16),
                           blocks=(256, 512), grids=(0, 2), tiles=(512, 2048))
+        elif a == "blocked" and not kw:
+            # narrow levels: large blocks cover a level or more
+            per[a] = tune(plan, b, x, algo=a, reps=reps, use_cache=use_cache,
+                          lanes=(1, 2, 4, 8), blocks=(512, 1024), grids=(0,),
+                          tiles=(512, 2048))
         else:
             per[a] = tune(plan, b, x, algo=a, reps=reps, use_cache=use_cache, **kw)
     name = min(per, key=lambda a: per[a]["best"][3])
     _apply(plan, per[name]["best"], name)
     plan.best_algo = name
     return {"algo": name, "best": per[name]["best"], "per_algo": per}
+
+
+def choice(result):
+    """The winning (algo, lanes, block, max_blocks, tile_rows, level_order) of
+    a ``tune_algos`` result, JSON-serialisable."""
+    best = result["best"]
+    return [result["algo"], int(best[0]), int(best[1]), int(best[2]), int(best[4]),
+            bool(best[5])]
+
+
+def apply_choice(plan, ch):
+    """Apply a ``choice`` to a plan without tuning; returns a result shaped
+    like ``tune_algos``'s (no timing)."""
+    algo, lanes, block, max_blocks, tile, order = ch
+    best = (lanes, block, max_blocks, float("nan"), tile, order)
+    _apply(plan, best, algo)
+    plan.best_algo = algo
+    return {"algo": algo, "best": best, "per_algo": {}}

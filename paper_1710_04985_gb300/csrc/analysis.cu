@@ -395,17 +395,15 @@ cudaError_t launch_histogram(const int* keys, int m, int* count, int bins,
 }
 
 // ------------------------------------------------------------ exclusive scan
-// One block of 1024 threads; thread t owns a contiguous chunk of the input.
-__global__ void __launch_bounds__(1024) exclusive_scan_k(const int* __restrict__ in, int* out,
-                                                         int m) {
-    __shared__ int warp_tot[32];
-    const int per = (m + 1023) / 1024;
-    const long long lo = (long long)threadIdx.x * per;
-    const long long hi = lo + per < m ? lo + per : m;
-    int s = 0;
-    for (long long e = lo; e < hi; ++e) s += in[e];
+// Exclusive scan in three coalesced phases: every block sums its chunk
+// (phase 1), one block scans the block sums (phase 2), every block scans its
+// chunk tile by tile with the chunk's offset as the carry-in (phase 3).
+constexpr int kScanThreads = 1024;
+constexpr int kScanBlocks = 1024;  // phase 2 scans these sums in one block
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int* warp_tot, int* total) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int incl = s;
+    int incl = v;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
         const int y = __shfl_up_sync(0xffffffffu, incl, off);
@@ -414,28 +412,86 @@ __global__ void __launch_bounds__(1024) exclusive_scan_k(const int* __restrict__
     if (lane == 31) warp_tot[w] = incl;
     __syncthreads();
     if (w == 0) {
-        const int v = warp_tot[lane];
-        int wi = v;
+        const int nw = blockDim.x >> 5;
+        const int t = lane < nw ? warp_tot[lane] : 0;
+        int wi = t;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, wi, off);
             if (lane >= off) wi += y;
         }
-        warp_tot[lane] = wi - v;
+        if (lane < nw) warp_tot[lane] = wi - t;
+        if (lane == 31) *total = wi;
     }
     __syncthreads();
-    int run = warp_tot[w] + incl - s;
-    for (long long e = lo; e < hi; ++e) {
-        const int v = in[e];
-        out[e] = run;
-        run += v;
-    }
-    if (threadIdx.x == 1023) out[m] = run;
+    const int r = warp_tot[w] + incl - v;
+    __syncthreads();  // warp_tot may be reused by the caller's next call
+    return r;
 }
 
+__global__ void __launch_bounds__(kScanThreads) scan_block_sums_k(const int* __restrict__ in,
+                                                                 int m, long long chunk,
+                                                                 int* sums) {
+    __shared__ int warp_tot[32];
+    __shared__ int total;
+    const long long lo = (long long)blockIdx.x * chunk;
+    const long long hi = lo + chunk < m ? lo + chunk : m;
+    int s = 0;
+    for (long long e = lo + threadIdx.x; e < hi; e += blockDim.x) s += in[e];
+    block_exclusive_scan(s, warp_tot, &total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_sums_k(int* sums, int nb) {
+    __shared__ int warp_tot[32];
+    __shared__ int total;
+    const int v = threadIdx.x < nb ? sums[threadIdx.x] : 0;
+    const int ex = block_exclusive_scan(v, warp_tot, &total);
+    if (threadIdx.x < nb) sums[threadIdx.x] = ex;
+    if (threadIdx.x == 0) sums[nb] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_chunks_k(const int* __restrict__ in,
+                                                             int* out, int m, long long chunk,
+                                                             const int* __restrict__ sums,
+                                                             int nb) {
+    __shared__ int warp_tot[32];
+    __shared__ int total;
+    const long long lo = (long long)blockIdx.x * chunk;
+    const long long hi = lo + chunk < m ? lo + chunk : m;
+    int carry = sums[blockIdx.x];
+    for (long long base = lo; base < hi; base += blockDim.x) {
+        const long long e = base + threadIdx.x;
+        const int v = e < hi ? in[e] : 0;
+        const int ex = block_exclusive_scan(v, warp_tot, &total);
+        if (e < hi) out[e] = carry + ex;
+        carry += total;
+    }
+    if (blockIdx.x == nb - 1 && threadIdx.x == 0) out[m] = sums[nb];
+}
+
+// out[0..m]: exclusive prefix sums of in[0..m-1], out[m] = total (in and
+// out must not overlap).  The block sums take at most kScanBlocks + 1 ints
+// of stream-ordered scratch (setup paths only; never under capture).
 cudaError_t launch_exclusive_scan(const int* in, int* out, int m, cudaStream_t s) {
-    exclusive_scan_k<<<1, 1024, 0, s>>>(in, out, m);
-    return cudaGetLastError();
+    if (m <= 0) {
+        return cudaMemsetAsync(out, 0, sizeof(int), s);
+    }
+    const long long per_block_min = kScanThreads;
+    long long nb = ((long long)m + per_block_min - 1) / per_block_min;
+    if (nb > kScanBlocks) nb = kScanBlocks;
+    long long chunk = ((long long)m + nb - 1) / nb;
+    chunk = (chunk + kScanThreads - 1) / kScanThreads * kScanThreads;
+    nb = ((long long)m + chunk - 1) / chunk;
+    int* sums = nullptr;
+    cudaError_t e = cudaMallocAsync(&sums, sizeof(int) * (size_t)(nb + 1), s);
+    if (e != cudaSuccess) return e;
+    scan_block_sums_k<<<(int)nb, kScanThreads, 0, s>>>(in, m, chunk, sums);
+    scan_sums_k<<<1, kScanThreads, 0, s>>>(sums, (int)nb);
+    scan_chunks_k<<<(int)nb, kScanThreads, 0, s>>>(in, out, m, chunk, sums, (int)nb);
+    e = cudaGetLastError();
+    cudaError_t f = cudaFreeAsync(sums, s);
+    return e != cudaSuccess ? e : f;
 }
 
 // ------------------------------------------------------------ radix sort

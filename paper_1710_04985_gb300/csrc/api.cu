@@ -56,6 +56,7 @@ struct Levels {
     // dependency count of every row and the working counters.
     int* count0 = nullptr;
     int* count = nullptr;
+    int method = SPTRSV_ANALYSIS_SWEEP;  // the analysis that produced these levels
 };
 
 struct DeviceGuard {
@@ -207,7 +208,7 @@ sptrsv_status_t level_sets(sptrsv_plan_t P, Levels& L, int nlev, cudaStream_t s)
 // each launch; the persistent form runs every level in one cooperative
 // launch.  Writes L.lev (allocated by the caller) and *nlev; synchronises s.
 sptrsv_status_t kahn_levels(sptrsv_plan_t P, const int* ptr, const int* idx, const int* dptr,
-                            const int* didx, bool persistent, Levels& L, int* nlev,
+                            const int* didx, bool persistent, bool probe, Levels& L, int* nlev,
                             cudaStream_t s) {
     const int n = P->n;
     int* scratch = nullptr;
@@ -215,24 +216,39 @@ sptrsv_status_t kahn_levels(sptrsv_plan_t P, const int* ptr, const int* idx, con
     // aligned and so comes first (cudaMalloc returns 256-byte aligned
     // memory); [2, 6) the queue end / rotating level counters (the roots are
     // counted in [2]; [5] = rows leveled by the persistent form); [6] level
-    // count; [7] pad; then count0, count, queue.
-    CK(cudaMalloc(&scratch, sizeof(int) * (3 * (size_t)n + 8)));
+    // count; [7, 10) the persistent form's narrow-run state; [10, 12) pad;
+    // then count0, count, queue.
+    CK(cudaMalloc(&scratch, sizeof(int) * (3 * (size_t)n + 12)));
     unsigned long long* arrivals = (unsigned long long*)scratch;
     int* qend = scratch + 2;
     int* nlev_dev = scratch + 6;
-    int* count0 = scratch + 8;
+    int* ctl = scratch + 7;
+    int* count0 = scratch + 12;
     int* count = count0 + n;
     int* queue = count + n;
-    cudaError_t e = cudaMemsetAsync(scratch, 0, 8 * sizeof(int), s);
+    cudaError_t e = cudaMemsetAsync(scratch, 0, 12 * sizeof(int), s);
     if (e == cudaSuccess) e = launch_column_counts(n, ptr, idx, count0, s);
     if (e == cudaSuccess) e = launch_kahn_roots(n, count0, count, L.lev, queue, qend, s);
     int h_last = 0, level = 0;
     if (e == cudaSuccess && persistent) {
-        const int block = 256;
-        long long grid = (long long)kahn_persistent_blocks_per_sm(block) * P->num_sms;
+        // One block of 1024 threads per SM keeps the grid barrier short (one
+        // arrival per SM); a level with at most one row per warp of a block
+        // runs on block 0 alone.
+        const int block = (int)env_ll("SPTRSV_KAHN_BLOCK", 1024);
+        long long per_sm = env_ll("SPTRSV_KAHN_BLOCKS_PER_SM", 1);
+        const long long fit = kahn_persistent_blocks_per_sm(block);
+        if (per_sm > fit) per_sm = fit;
+        long long grid = per_sm * P->num_sms;
         if (grid < 1) grid = 1;
-        e = launch_kahn_persistent(dptr, didx, count, L.lev, queue, qend, n, arrivals, nlev_dev,
-                                   P->status, P->spin.limit, (int)grid, block, s);
+        const int narrow = (int)env_ll("SPTRSV_KAHN_NARROW", block / 32);
+        // Probe (automatic method only): after 256 levels, fewer than 112
+        // rows per level on average means a deep, narrow graph, where a
+        // grid barrier per level loses to the sweep (measured: 2.2-3.1 us
+        // per level against the sweep's 1.2-1.3 us on such graphs).
+        const int probe_level = probe ? 256 : 0;
+        e = launch_kahn_persistent(dptr, didx, count, L.lev, queue, qend, ctl, n, narrow,
+                                   probe_level, 112, arrivals, nlev_dev, P->status,
+                                   P->spin.limit, (int)grid, block, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&level, nlev_dev, sizeof(int),
                                                   cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&h_last, qend + 3, sizeof(int),
@@ -259,6 +275,10 @@ sptrsv_status_t kahn_levels(sptrsv_plan_t P, const int* ptr, const int* idx, con
     if (e != cudaSuccess) return cuda_fail(e);
     int row = -1;
     ST(take_status(P, s, &row));
+    if (probe && level == -1) {  // gave up early: the caller runs the sweep
+        *nlev = -1;
+        return SPTRSV_OK;
+    }
     if (h_last != n || level < 1) return SPTRSV_ERR_INTERNAL;  // every row must be leveled
     *nlev = level;
     return SPTRSV_OK;
@@ -268,17 +288,29 @@ sptrsv_status_t kahn_levels(sptrsv_plan_t P, const int* ptr, const int* idx, con
 // Kahn's algorithm given the dependents' structure dptr/didx), then the
 // bucket sort into level sets.  Synchronises s.
 sptrsv_status_t build_levels(sptrsv_plan_t P, const int* ptr, const int* idx, bool upper,
-                             Levels& L, cudaStream_t s, int method = SPTRSV_ANALYSIS_SWEEP,
+                             Levels& L, cudaStream_t s, int method = SPTRSV_ANALYSIS_AUTO,
                              const int* dptr = nullptr, const int* didx = nullptr) {
     const int n = P->n;
     CK(cudaMalloc(&L.lev, sizeof(int) * (size_t)n));
     CK(cudaMemsetAsync(L.lev, 0xff, sizeof(int) * (size_t)n, s));
     CK(cudaMemsetAsync(P->counters, 0, 2 * sizeof(int), s));
-    int nlev = 0;
-    if (method == SPTRSV_ANALYSIS_KAHN_HOST_LOOP || method == SPTRSV_ANALYSIS_KAHN_PERSISTENT) {
-        ST(kahn_levels(P, ptr, idx, dptr, didx, method == SPTRSV_ANALYSIS_KAHN_PERSISTENT, L,
-                       &nlev, s));
-    } else {
+    int nlev = -1;
+    const bool kahn = method == SPTRSV_ANALYSIS_KAHN_HOST_LOOP ||
+                      method == SPTRSV_ANALYSIS_KAHN_PERSISTENT ||
+                      (method == SPTRSV_ANALYSIS_AUTO && dptr);
+    L.method = SPTRSV_ANALYSIS_SWEEP;
+    if (kahn) {
+        ST(kahn_levels(P, ptr, idx, dptr, didx, method != SPTRSV_ANALYSIS_KAHN_HOST_LOOP,
+                       method == SPTRSV_ANALYSIS_AUTO, L, &nlev, s));
+        if (nlev >= 0)
+            L.method = method == SPTRSV_ANALYSIS_KAHN_HOST_LOOP ? SPTRSV_ANALYSIS_KAHN_HOST_LOOP
+                                                                : SPTRSV_ANALYSIS_KAHN_PERSISTENT;
+    }
+    if (nlev < 0) {  // the sweep, by choice or after Kahn gave up
+        if (kahn) {
+            CK(cudaMemsetAsync(L.lev, 0xff, sizeof(int) * (size_t)n, s));
+            CK(cudaMemsetAsync(P->counters, 0, 2 * sizeof(int), s));
+        }
         ST(sweep_levels(P, ptr, idx, upper, L, &nlev, s));
     }
     return level_sets(P, L, nlev, s);
@@ -369,7 +401,8 @@ sptrsv_status_t build_transpose(sptrsv_plan_t P, cudaStream_t s) {
     if (P->has_trans) return SPTRSV_OK;
     if (capturing(s)) return SPTRSV_ERR_NOT_SUPPORTED;
     ST(build_transpose_pattern(P, s));
-    ST(build_levels(P, P->tptr, P->tidx, !P->upper, P->trn, s));
+    ST(build_levels(P, P->tptr, P->tidx, !P->upper, P->trn, s, SPTRSV_ANALYSIS_AUTO, P->rowptr,
+                    P->colidx));
     P->has_trans = true;
     return SPTRSV_OK;
 }
@@ -624,7 +657,9 @@ sptrsv_status_t run_solve(sptrsv_plan_t P, bool trans, bool f64, const void* val
     const int lanes = mrhs ? mrhs_lanes(nrhs) : P->lanes;
     if (algo == SPTRSV_ALGO_SELF_CHAINS && !mrhs) ST(build_chain(P, trans, lanes, s));
     // the level-ordered copy holds the plan's own element type
-    const bool permuted = algo == SPTRSV_ALGO_SELF_PERMUTED && !mrhs && f64 == P->f64;
+    const bool blocked = algo == SPTRSV_ALGO_SELF_BLOCKED && !mrhs && f64 == P->f64;
+    const bool permuted =
+        (algo == SPTRSV_ALGO_SELF_PERMUTED || blocked) && !mrhs && f64 == P->f64;
     if (permuted) ST(build_permuted(P, trans, s));
     const bool column = algo == SPTRSV_ALGO_SELF_COLUMN && !mrhs;
     if (column) ST(build_column(P, trans, s));
@@ -698,13 +733,26 @@ sptrsv_status_t run_solve(sptrsv_plan_t P, bool trans, bool f64, const void* val
         const int R = 32 / lanes;
         const long long tickets = ((long long)P->n + R - 1) / R;
         const long long want_blocks = (tickets + P->block / 32 - 1) / (P->block / 32);
-        long long grid = (long long)self_perm_blocks_per_sm(f64, lanes, P->block) * P->num_sms;
-        if (P->max_blocks > 0 && grid > P->max_blocks) grid = P->max_blocks;
-        if (grid > want_blocks) grid = want_blocks;
-        if (grid < 1) grid = 1;
-        ST(prof_begin(P, s));
-        CK(launch_self_k1(f64, lanes, p, (int)grid, P->block, s));
-        ST(prof_end(P, s));
+        if (blocked) {
+            const long long tiles = ((long long)P->n + P->tile_rows - 1) / P->tile_rows;
+            long long grid = (long long)blocked_blocks_per_sm(f64, lanes, P->block, P->tile_rows) *
+                             P->num_sms;
+            if (P->max_blocks > 0 && grid > P->max_blocks) grid = P->max_blocks;
+            if (grid > tiles) grid = tiles;
+            if (grid < 1) grid = 1;
+            ST(prof_begin(P, s));
+            CK(launch_blocked_k1(f64, lanes, p, P->tile_rows, (int)grid, P->block, s));
+            ST(prof_end(P, s));
+        } else {
+            long long grid =
+                (long long)self_perm_blocks_per_sm(f64, lanes, P->block) * P->num_sms;
+            if (P->max_blocks > 0 && grid > P->max_blocks) grid = P->max_blocks;
+            if (grid > want_blocks) grid = want_blocks;
+            if (grid < 1) grid = 1;
+            ST(prof_begin(P, s));
+            CK(launch_self_k1(f64, lanes, p, (int)grid, P->block, s));
+            ST(prof_end(P, s));
+        }
         launches = 2;
     } else {
         const size_t esize = f64 ? sizeof(double) : sizeof(float);
@@ -761,7 +809,7 @@ sptrsv_status_t solve_common(sptrsv_plan_t P, bool trans, const void* b, void* x
     if (!P || nrhs < 1 || ld < nrhs ||
         (algo != SPTRSV_ALGO_LEVEL && algo != SPTRSV_ALGO_SELF && algo != SPTRSV_ALGO_SELF_TILED &&
          algo != SPTRSV_ALGO_SELF_CHAINS && algo != SPTRSV_ALGO_SELF_PERMUTED &&
-         algo != SPTRSV_ALGO_SELF_COLUMN))
+         algo != SPTRSV_ALGO_SELF_COLUMN && algo != SPTRSV_ALGO_SELF_BLOCKED))
         return SPTRSV_ERR_INVALID_ARG;
     P->last_launches = 0;
     if (P->n == 0) return SPTRSV_OK;
@@ -828,7 +876,14 @@ sptrsv_status_t sptrsv_analyze(int n, int nnz, const int* d_rowptr, const int* d
         int row = -1;
         if (rc == SPTRSV_OK) rc = take_status(P, s, &row);
         if (rc == SPTRSV_ERR_STRUCTURE || rc == SPTRSV_ERR_ZERO_PIVOT) g_last_error_row = row;
-        if (rc == SPTRSV_OK) rc = build_levels(P, d_rowptr, d_colidx, P->upper, P->fwd, s);
+        // Setup (Table 1): the transposed pattern (TRANS_GPU; also the column
+        // structure of the transposed and column-wise solves), then the
+        // levels by the automatic method: Kahn's algorithm in one launch,
+        // falling back to the sweep on deep, narrow graphs.
+        if (rc == SPTRSV_OK) rc = build_transpose_pattern(P, s);
+        if (rc == SPTRSV_OK)
+            rc = build_levels(P, d_rowptr, d_colidx, P->upper, P->fwd, s, SPTRSV_ANALYSIS_AUTO,
+                              P->tptr, P->tidx);
     }
     if (rc != SPTRSV_OK) {
         destroy(P);
@@ -844,7 +899,7 @@ sptrsv_status_t sptrsv_reanalyze(sptrsv_plan_t plan, int transpose, sptrsv_analy
                                  void* stream) {
     if (!plan || (transpose != 0 && transpose != 1) ||
         (method != SPTRSV_ANALYSIS_SWEEP && method != SPTRSV_ANALYSIS_KAHN_HOST_LOOP &&
-         method != SPTRSV_ANALYSIS_KAHN_PERSISTENT))
+         method != SPTRSV_ANALYSIS_KAHN_PERSISTENT && method != SPTRSV_ANALYSIS_AUTO))
         return SPTRSV_ERR_INVALID_ARG;
     sptrsv_plan_t P = plan;
     if (P->n == 0) return SPTRSV_OK;
@@ -886,6 +941,13 @@ sptrsv_status_t sptrsv_reanalyze(sptrsv_plan_t plan, int transpose, sptrsv_analy
     L.count0 = L.count = nullptr;
     free_levels(L);
     L = std::move(fresh);
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t sptrsv_analysis_method(sptrsv_plan_t plan, int transpose, int* method) {
+    if (!plan || !method || (transpose != 0 && transpose != 1)) return SPTRSV_ERR_INVALID_ARG;
+    if (transpose && !plan->has_trans && plan->n > 0) return SPTRSV_ERR_NOT_SUPPORTED;
+    *method = (transpose ? plan->trn : plan->fwd).method;
     return SPTRSV_OK;
 }
 

@@ -80,6 +80,12 @@ cudaError_t launch_prep_column(bool f64, const SolveParams& p, const ColumnParam
 cudaError_t launch_column_k1(bool f64, int lanes, const SolveParams& p, const ColumnParams& c,
                              int grid, int block, cudaStream_t s);
 int column_blocks_per_sm(bool f64, int lanes, bool cmap, int block);
+// Blocked self-scheduled solve on the level-ordered copy (solve_blocked.cu):
+// a block per tile of tile_rows consecutive positions, in-tile dependencies
+// through shared memory (tile_rows * element size <= 48 KB - 256 B).
+cudaError_t launch_blocked_k1(bool f64, int lanes, const SolveParams& p, int tile_rows, int grid,
+                              int block, cudaStream_t s);
+int blocked_blocks_per_sm(bool f64, int lanes, int block, int tile_rows);
 // Resident blocks per SM of the level-ordered-copy form of self_solve_k1.
 int self_perm_blocks_per_sm(bool f64, int lanes, int block);
 
@@ -152,11 +158,16 @@ cudaError_t launch_kahn_level(const int* dptr, const int* didx, int* count, int*
                               unsigned long long* status, int max_grid, cudaStream_t s);
 int kahn_persistent_blocks_per_sm(int block);
 // cnt[0] = roots queued by launch_kahn_roots, cnt[1] = cnt[2] = 0; on exit
-// cnt[3] = rows leveled and *nlev_out = levels.
+// cnt[3] = rows leveled and *nlev_out = levels.  ctl: 3 ints of scratch.
+// Levels of at most `narrow` rows run on block 0 alone.  With probe_level
+// > 0, the launch gives up (*nlev_out = -1) when fewer than
+// probe_level * probe_min_avg rows are leveled after probe_level levels.
 cudaError_t launch_kahn_persistent(const int* dptr, const int* didx, int* count, int* lev,
-                                   int* queue, int* cnt, int n, unsigned long long* arrivals,
-                                   int* nlev_out, unsigned long long* status, long long limit,
-                                   int grid, int block, cudaStream_t s);
+                                   int* queue, int* cnt, int* ctl, int n, int narrow,
+                                   int probe_level, int probe_min_avg,
+                                   unsigned long long* arrivals, int* nlev_out,
+                                   unsigned long long* status, long long limit, int grid,
+                                   int block, cudaStream_t s);
 
 // ---- auxiliary kernels (aux.cu)
 cudaError_t launch_grad_vals(bool f64, int lanes, int n, const int* ptr, const int* idx, bool unit,

@@ -127,47 +127,121 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* arrivals,
     return s_ok != 0;
 }
 
+// Removes the frontier queue[base, base + size) of level `level` with the
+// warps [w0, w0 + nw): a warp per frontier row, its lanes over the row's
+// outgoing edges; roots of level + 1 are counted in *tail and stored after
+// the frontier.  Queue entries may have been written by other SMs: they are
+// read from L2 (__ldcg), never from a stale L1 line.
+__device__ __forceinline__ void kahn_frontier(const int* __restrict__ dptr,
+                                              const int* __restrict__ didx, int* count, int* lev,
+                                              int* queue, int* tail, int n, long long base,
+                                              int size, int level, long long w0, long long nw,
+                                              int lane, unsigned long long* status) {
+    int* next = queue + base + size;
+    for (long long w = w0; w < size; w += nw) {
+        const int i = __ldcg(queue + base + w);
+        const int beg = dptr[i], end = dptr[i + 1];
+        for (int q = beg + lane; q < end; q += 32) {
+            const int r = didx[q];
+            if (r == i) continue;
+            if (atomicSub(count + r, 1) == 1) {
+                lev[r] = level + 1;
+                const int at = atomicAdd(tail, 1);
+                if (base + size + at < n) next[at] = r;
+                else report(status, r, kCodeInternal);
+            }
+        }
+    }
+}
+
 // Persistent driver.  The frontier of level L is queue[base_L, base_L +
 // size_L); its removal appends the roots of level L + 1 right after it.
-// Level sizes live in three rotating counters cnt[L % 3]: the value a block
-// reads after a barrier must not move while slower blocks still read it, so
-// the roots of level L + 1 are counted in cnt[(L+1) % 3] (not in the one
-// being read), and block 0 clears cnt[(L+2) % 3] during level L: every block
-// read that counter (size of level L - 1) before arriving at the barrier
-// that opened level L, and nobody appends to it before the next barrier.
-// cnt[0] holds the roots queued by kahn_roots_k; cnt[1] and cnt[2] start at
-// zero.  Stops when a level exposes no new root and writes the level count.
+// Level sizes live in three rotating counters cnt[L % 3]: the value read
+// after a barrier must not move while slower readers still read it, so the
+// roots of level L + 1 are counted in cnt[(L+1) % 3] (not in the one being
+// read), and block 0 clears cnt[(L+2) % 3] at the start of level L: every
+// reader read that counter (size of level L - 1) before the barrier that
+// opened level L, and nobody appends to it before the next one.
+//
+// Wide levels run on the whole grid, one grid barrier each.  A level of at
+// most `narrow` rows runs on block 0 alone, which keeps going through
+// consecutive narrow levels separated only by block barriers (no grid-wide
+// step) and then publishes (base, size, level) in ctl[0..2]; the other
+// blocks meanwhile wait at the one grid barrier that closes the run.  Deep,
+// narrow dependency graphs thus cost a block barrier per level, not a grid
+// barrier.  cnt[0] holds the roots queued by kahn_roots_k; cnt[1], cnt[2]
+// start at zero.  Writes the level count and cnt[3] = rows leveled.
+constexpr int kNarrowRun = 4096;
+
 __global__ void kahn_persistent_k(const int* __restrict__ dptr, const int* __restrict__ didx,
-                                  int* count, int* lev, int* queue, int* cnt, int n,
+                                  int* count, int* lev, int* queue, int* cnt, int* ctl, int n,
+                                  int narrow, int probe_level, int probe_min_avg,
                                   unsigned long long* arrivals, int* nlev_out,
                                   unsigned long long* status, long long limit) {
     const int lane = threadIdx.x & 31;
     const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
     const long long wid = (((long long)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5);
+    const int bwarps = blockDim.x >> 5, bwid = threadIdx.x >> 5;
     unsigned long long gen = 0;
     long long base = 0;
     int size = *(volatile int*)cnt;  // roots, queued before this launch
     int level = 0;
+    bool probed = probe_level <= 0;
     while (size > 0) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) cnt[(level + 2) % 3] = 0;
-        int* tail = cnt + (level + 1) % 3;
-        int* next = queue + base + size;  // where the roots of level + 1 go
-        // queue entries of this frontier were written by other SMs during the
-        // previous level: read them from L2 (__ldcg), never from a stale L1 line
-        for (long long w = wid; w < size; w += warps) {
-            const int i = __ldcg(queue + base + w);
-            const int beg = dptr[i], end = dptr[i + 1];
-            for (int q = beg + lane; q < end; q += 32) {
-                const int r = didx[q];
-                if (r == i) continue;
-                if (atomicSub(count + r, 1) == 1) {
-                    lev[r] = level + 1;
-                    const int at = atomicAdd(tail, 1);
-                    if (base + size + at < n) next[at] = r;
-                    else report(status, r, kCodeInternal);
-                }
+        // Early exit for deep, narrow graphs (a grid barrier per level costs
+        // more there than the sweep): every block sees the same (base,
+        // level) here, so all of them decide alike.
+        if (!probed && level >= probe_level) {
+            probed = true;
+            if (base < (long long)level * probe_min_avg) {
+                if (blockIdx.x == 0 && threadIdx.x == 0) *nlev_out = -1;
+                return;
             }
         }
+        if (size <= narrow) {
+            if (blockIdx.x == 0) {
+                // at most kNarrowRun levels per run, so the other blocks' wait
+                // at the closing barrier stays far below its spin limit; a run
+                // also stops at the probe level so that the probe is taken
+                for (int run = 0; run < kNarrowRun && size > 0 && size <= narrow &&
+                                   (probed || level < probe_level);
+                     ++run) {
+                    if (threadIdx.x == 0) cnt[(level + 2) % 3] = 0;
+                    __syncthreads();
+                    int* tail = cnt + (level + 1) % 3;
+                    kahn_frontier(dptr, didx, count, lev, queue, tail, n, base, size, level, bwid,
+                                  bwarps, lane, status);
+                    __syncthreads();  // every append of this level has been performed
+                    int nsz;
+                    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(nsz) : "l"(tail)
+                                 : "memory");
+                    __syncthreads();  // read by all before the next level appends
+                    base += size;
+                    size = nsz;
+                    ++level;
+                }
+                if (threadIdx.x == 0) {
+                    ctl[0] = (int)base;
+                    ctl[1] = size;
+                    ctl[2] = level;
+                }
+            }
+            ++gen;
+            if (!grid_barrier(arrivals, gen * gridDim.x, limit, status, level)) return;
+            int st[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(st[k]) : "l"(ctl + k)
+                             : "memory");
+            base = st[0];
+            size = st[1];
+            level = st[2];
+            continue;
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) cnt[(level + 2) % 3] = 0;
+        int* tail = cnt + (level + 1) % 3;
+        kahn_frontier(dptr, didx, count, lev, queue, tail, n, base, size, level, wid, warps, lane,
+                      status);
         ++gen;
         if (!grid_barrier(arrivals, gen * gridDim.x, limit, status, level)) return;
         int nsz;
@@ -192,12 +266,16 @@ int kahn_persistent_blocks_per_sm(int block) {
 }
 
 cudaError_t launch_kahn_persistent(const int* dptr, const int* didx, int* count, int* lev,
-                                   int* queue, int* cnt, int n, unsigned long long* arrivals,
-                                   int* nlev_out, unsigned long long* status, long long limit,
-                                   int grid, int block, cudaStream_t s) {
-    void* args[] = {(void*)&dptr, (void*)&didx, (void*)&count,    (void*)&lev,
-                    (void*)&queue, (void*)&cnt,  (void*)&n,        (void*)&arrivals,
-                    (void*)&nlev_out, (void*)&status, (void*)&limit};
+                                   int* queue, int* cnt, int* ctl, int n, int narrow,
+                                   int probe_level, int probe_min_avg,
+                                   unsigned long long* arrivals, int* nlev_out,
+                                   unsigned long long* status, long long limit, int grid,
+                                   int block, cudaStream_t s) {
+    void* args[] = {(void*)&dptr,        (void*)&didx,          (void*)&count,
+                    (void*)&lev,         (void*)&queue,         (void*)&cnt,
+                    (void*)&ctl,         (void*)&n,             (void*)&narrow,
+                    (void*)&probe_level, (void*)&probe_min_avg, (void*)&arrivals,
+                    (void*)&nlev_out,    (void*)&status,        (void*)&limit};
     return cudaLaunchCooperativeKernel((const void*)kahn_persistent_k, dim3(grid), dim3(block),
                                        args, 0, s);
 }

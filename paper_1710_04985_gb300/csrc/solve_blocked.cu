@@ -1,0 +1,267 @@
+// Blocked self-scheduled solve (SPTRSV_ALGO_SELF_BLOCKED), one right-hand
+// side, on the plan's level-ordered copy.
+//
+// When levels are narrow (tens to hundreds of rows), a solve is a long chain
+// of small steps and every step of Alg. 3 pays an L2 handshake (~0.6-0.8 us
+// on GB300).  In level order consecutive levels are consecutive positions,
+// so a tile of T consecutive positions holds many whole levels, and most
+// dependencies of a row point into the same tile.  A thread block takes a
+// tile (tickets, as rows are taken in Alg. 3) and:
+//  * serves a dependency inside the tile from a shared-memory copy of the
+//    tile's results (Sec. 4.3 remark 2: consecutive warps on consecutive
+//    unknowns make shared-memory partial results possible once the matrix is
+//    preordered by level); dependencies on earlier tiles are polled in the
+//    position-ordered publication buffer in global memory, as in Alg. 3;
+//  * hands its warps groups of 32/W consecutive positions from a
+//    shared-memory counter, so a slow group holds back only the rows that
+//    really depend on it;
+//  * prefetches the tile's rows into L2 as soon as it takes the tile: the
+//    tile a block takes next lies far ahead of the dependency frontier, so
+//    its loads become L2 hits by the time the frontier arrives.
+// A block starts its next tile only when every group of the current one is
+// done (one block barrier per tile); that tile is not yet on the critical
+// path when this happens.  Deadlock freedom: a group waits only on earlier
+// positions, i.e. on groups of this tile taken earlier by running warps of
+// this block or on earlier tiles held by running blocks.  Every wait is
+// bounded.  Each row is reduced in the same order as in the other
+// self-scheduled forms, so results are bitwise equal for the same sub-warp
+// width.
+#include "internal.h"
+
+namespace sptrsv {
+
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+template <typename T>
+__device__ __forceinline__ T lds_volatile(const T* p) {
+    return *(const volatile T*)p;
+}
+template <typename T>
+__device__ __forceinline__ void sts_volatile(T* p, T v) {
+    *(volatile T*)p = v;
+}
+
+template <typename T, int W>
+__global__ void __launch_bounds__(1024) blocked_solve_k1(SolveParams p, int tile_rows) {
+    extern __shared__ __align__(16) unsigned char blocked_smem[];
+    T* xs = (T*)blocked_smem;
+    __shared__ int s_tile;
+    __shared__ int s_next;
+    constexpr int R = 32 / W;
+    constexpr int E = kChunk;
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int grp = lane / W;
+    const int sl = lane - grp * W;
+    const unsigned gmask = group_mask<W>(lane);
+    const T* __restrict__ vals = (const T*)p.vals;  // level-ordered copy
+    const T* b = (const T*)p.b;
+    T* x = (T*)p.x;
+    T* xp = (T*)p.xp;  // publication buffer, position order
+    const int n = p.n;
+    while (true) {
+        if (threadIdx.x == 0) {
+            s_tile = atomicAdd(p.ticket, 1);
+            s_next = 0;
+        }
+        __syncthreads();
+        const long long p0 = (long long)s_tile * tile_rows;
+        if (p0 >= n) break;
+        const int in_tile = (int)((n - p0) < tile_rows ? (n - p0) : tile_rows);
+        for (int k = threadIdx.x; k < in_tile; k += blockDim.x) xs[k] = Marker<T>::pending_value();
+        {  // the tile's rows are contiguous in the copy: one L2 prefetch per 128 B line
+            const long long q0 = p.ptr[p0], q1 = p.ptr[p0 + in_tile];
+            for (long long q = q0 + 32ll * threadIdx.x; q < q1; q += 32ll * blockDim.x)
+                prefetch_l2(p.idx + q);
+            for (long long q = q0 + (128 / sizeof(T)) * threadIdx.x; q < q1;
+                 q += (long long)(128 / sizeof(T)) * blockDim.x)
+                prefetch_l2(vals + q);
+        }
+        __syncthreads();
+        const int groups = (in_tile + R - 1) / R;
+        while (true) {
+            int g = 0;
+            if (lane == 0) g = atomicAdd(&s_next, 1);
+            g = __shfl_sync(FULL, g, 0);
+            if (g >= groups) break;
+            const int off = g * R + grp;  // this lane group's position in the tile
+            const long long k = p0 + off;
+            const bool has_row = off < in_tile;
+            int i = 0, beg = 0, end = 0;
+            T dinv = T(1), sum = T(0);
+            if (has_row) {
+                i = p.jlev[k];
+                beg = p.ptr[k];
+                end = p.ptr[k + 1];
+                if (sl == 0) {  // same arithmetic as the other self-scheduled forms
+                    if (!p.unit) {
+                        const int q = p.diag_first ? beg : end - 1;
+                        dinv = T(1) / vals[q];
+                    }
+                    sum = b[(long long)i * p.ldb];
+                    if (!p.unit) sum *= dinv;
+                }
+            }
+            if (W > 1 && !p.unit) dinv = __shfl_sync(FULL, dinv, grp * W);
+            int q0 = beg + sl;
+            int c[E];  // position of the dependency, or its offset in the tile
+            T a[E], v[E];
+            unsigned live = 0, pend = 0, local = 0;
+            auto load_chunk = [&]() {
+                live = pend = local = 0;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int q = q0 + e * W;
+                    c[e] = -1;
+                    a[e] = T(0);
+                    v[e] = T(0);
+                    if (q < end) {
+                        const int cc = p.idx[q];
+                        if (cc != (int)k) {
+                            a[e] = vals[q];
+                            live |= 1u << e;
+                            if (cc >= p0) {
+                                c[e] = (int)(cc - p0);
+                                local |= 1u << e;
+                            } else {
+                                c[e] = cc;
+                            }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    if (!(live & (1u << e))) continue;
+                    v[e] = (local & (1u << e)) ? lds_volatile(xs + c[e]) : ld_relaxed(xp + c[e]);
+                }
+                if (!p.unit) {
+#pragma unroll
+                    for (int e = 0; e < E; ++e)
+                        if (live & (1u << e)) a[e] *= dinv;
+                }
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    if ((live & (1u << e)) && Marker<T>::pending(v[e])) pend |= 1u << e;
+            };
+            bool lane_done = q0 >= end;
+            if (!lane_done) load_chunk();
+            bool published = !has_row;
+            long long waits = 0;
+            unsigned ns = 32;
+            while (true) {
+                if (!lane_done && pend == 0) {
+                    sum = fold_chunk(sum, a, v, live);
+                    q0 += W * E;
+                    if (q0 >= end) lane_done = true;
+                    else load_chunk();
+                }
+                const unsigned done = __ballot_sync(FULL, lane_done);
+                const bool fresh = !published && (done & gmask) == gmask;
+                if (__any_sync(FULL, fresh)) {
+                    const T tot = group_sum<W>(sum, FULL);
+                    if (fresh && sl == 0 && i != p.withhold) {
+                        const T xi = publishable(tot);
+                        sts_volatile(xs + off, xi);
+                        st_relaxed(xp + k, xi);
+                        x[(long long)i * p.ldx] = xi;
+                    }
+                }
+                published = published || fresh;
+                if (__all_sync(FULL, published)) break;
+                if (__any_sync(FULL, !lane_done && pend == 0)) continue;  // fold first
+                if (__any_sync(FULL, pend != 0)) {
+                    // Tight wait: re-poll the pending entries (shared memory or
+                    // the publication buffer) until something arrives.
+                    const unsigned before = pend;
+                    do {
+#pragma unroll
+                        for (int e = 0; e < E; ++e) {
+                            if (!(pend & (1u << e))) continue;
+                            v[e] = (local & (1u << e)) ? lds_volatile(xs + c[e])
+                                                       : ld_relaxed(xp + c[e]);
+                        }
+#pragma unroll
+                        for (int e = 0; e < E; ++e)
+                            if ((pend & (1u << e)) && !Marker<T>::pending(v[e]))
+                                pend &= ~(1u << e);
+                        if (++waits >= p.spin.limit) {
+                            if (pend) {
+                                report(p.status, i, kCodeTimeout);
+#pragma unroll
+                                for (int e = 0; e < E; ++e)
+                                    if (pend & (1u << e)) v[e] = Marker<T>::canonical_nan();
+                                pend = 0;
+                            }
+                            waits = 0;
+                            break;
+                        }
+                        if (__any_sync(FULL, pend != before)) break;
+                        if (waits >= p.spin.hot && __any_sync(FULL, (pend & ~local) != 0)) {
+                            __nanosleep(ns);  // back off only while an L2 dependency is pending
+                            ns = ns < p.spin.max_ns ? ns * 2 : p.spin.max_ns;
+                        }
+                    } while (true);
+                } else {
+                    waits = 0;
+                    ns = 32;
+                }
+            }
+        }
+        __syncthreads();  // every group of the tile is done before xs is reused
+    }
+}
+
+template <typename T, int W>
+static cudaError_t blocked_w(const SolveParams& p, int tile_rows, int grid, int block,
+                             cudaStream_t s) {
+    const size_t smem = sizeof(T) * (size_t)tile_rows;  // <= 48 KB, checked by the caller
+    blocked_solve_k1<T, W><<<grid, block, smem, s>>>(p, tile_rows);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t blocked_t(int lanes, const SolveParams& p, int tile_rows, int grid, int block,
+                             cudaStream_t s) {
+    switch (lanes) {
+        case 1: return blocked_w<T, 1>(p, tile_rows, grid, block, s);
+        case 2: return blocked_w<T, 2>(p, tile_rows, grid, block, s);
+        case 4: return blocked_w<T, 4>(p, tile_rows, grid, block, s);
+        case 8: return blocked_w<T, 8>(p, tile_rows, grid, block, s);
+        case 16: return blocked_w<T, 16>(p, tile_rows, grid, block, s);
+        case 32: return blocked_w<T, 32>(p, tile_rows, grid, block, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_blocked_k1(bool f64, int lanes, const SolveParams& p, int tile_rows, int grid,
+                              int block, cudaStream_t s) {
+    return f64 ? blocked_t<double>(lanes, p, tile_rows, grid, block, s)
+               : blocked_t<float>(lanes, p, tile_rows, grid, block, s);
+}
+
+template <typename T>
+static int occ_blocked(int lanes, int block, size_t smem) {
+    int nb = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+#define SPTRSV_OCC(WW) \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, blocked_solve_k1<T, WW>, block, smem)
+    switch (lanes) {
+        case 1: SPTRSV_OCC(1); break;
+        case 2: SPTRSV_OCC(2); break;
+        case 4: SPTRSV_OCC(4); break;
+        case 8: SPTRSV_OCC(8); break;
+        case 16: SPTRSV_OCC(16); break;
+        case 32: SPTRSV_OCC(32); break;
+    }
+#undef SPTRSV_OCC
+    return (e == cudaSuccess && nb > 0) ? nb : 1;
+}
+
+int blocked_blocks_per_sm(bool f64, int lanes, int block, int tile_rows) {
+    const size_t smem = (f64 ? 8 : 4) * (size_t)tile_rows;
+    return f64 ? occ_blocked<double>(lanes, block, smem) : occ_blocked<float>(lanes, block, smem);
+}
+
+}  // namespace sptrsv

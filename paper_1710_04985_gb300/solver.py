@@ -16,7 +16,7 @@ from ._lib import SptrsvError, check
 
 ALGOS = {"level": _lib.ALGO_LEVEL, "self": _lib.ALGO_SELF, "tiled": _lib.ALGO_SELF_TILED,
          "chains": _lib.ALGO_SELF_CHAINS, "permuted": _lib.ALGO_SELF_PERMUTED,
-         "column": _lib.ALGO_SELF_COLUMN}
+         "column": _lib.ALGO_SELF_COLUMN, "blocked": _lib.ALGO_SELF_BLOCKED}
 
 
 def _ptr(t):
@@ -201,15 +201,23 @@ class TriangularPlan:
               "sptrsv_refresh_values")
 
     ANALYSIS = {"sweep": _lib.ANALYSIS_SWEEP, "kahn_host_loop": _lib.ANALYSIS_KAHN_HOST_LOOP,
-                "kahn_persistent": _lib.ANALYSIS_KAHN_PERSISTENT}
+                "kahn_persistent": _lib.ANALYSIS_KAHN_PERSISTENT, "auto": _lib.ANALYSIS_AUTO}
 
-    def reanalyze(self, method="sweep", transpose=False, stream=None):
+    def reanalyze(self, method="auto", transpose=False, stream=None):
         """Recompute the levels of the forward (or transposed) system with
         ``method`` ("sweep", "kahn_host_loop" as in Sec. 4.4.1,
-        "kahn_persistent"); returns the analysis time in ms."""
+        "kahn_persistent", or "auto" as the plan's own setup); returns the
+        analysis time in ms."""
         check(_lib.load().sptrsv_reanalyze(self._h, int(bool(transpose)), self.ANALYSIS[method],
                                            _stream_handle(stream)), "sptrsv_reanalyze")
         return self.analysis_ms
+
+    def analysis_method(self, transpose=False):
+        """Name of the analysis that produced the current levels."""
+        m = ctypes.c_int()
+        check(_lib.load().sptrsv_analysis_method(self._h, int(bool(transpose)),
+                                                 ctypes.byref(m)), "sptrsv_analysis_method")
+        return {v: k for k, v in self.ANALYSIS.items()}[m.value]
 
     # ------------------------------------------------------------ tuning
     def set_tuning(self, lanes_per_row, block_size=256, max_blocks=0):

@@ -79,7 +79,22 @@ def test_transpose_levels_and_pattern(name):
         assert np.array_equal(A.vals[tmap], T.data)
 
 
-@pytest.mark.parametrize("method", ["kahn_host_loop", "kahn_persistent", "sweep"])
+def test_automatic_analysis_choice():
+    """The plan's own setup (SPTRSV_ANALYSIS_AUTO) levels wide graphs with
+    Kahn's algorithm in one launch and gives up on deep, narrow ones after
+    256 levels, falling back to the sweep; the levels are the same."""
+    for name, want in (("ilu_L", "kahn_persistent"), ("lap3d_27pt", "kahn_persistent"),
+                       ("bidiag", "sweep"), ("bidiag_upper", "sweep")):
+        A = mat(name)
+        with plan_for(A) as p:
+            assert p.analysis_method() == want, name
+            assert_levels_equal(p.levels(), A)
+            p.prepare_transpose()
+            assert p.analysis_method(transpose=True) == want, name
+            assert_levels_equal(p.levels(transpose=True), A, transpose=True)
+
+
+@pytest.mark.parametrize("method", ["kahn_host_loop", "kahn_persistent", "sweep", "auto"])
 @pytest.mark.parametrize("name", ["workload0", "ilu_L", "ilu_U", "general", "general_upper",
                                   "bidiag", "diag", "long_rows", "unit_nodiag", "lap3d_27pt"])
 def test_reanalyze_methods_give_the_same_levels(name, method):
@@ -105,7 +120,7 @@ def test_reanalyze_methods_give_the_same_levels(name, method):
 # ---------------------------------------------------------------- solves
 
 @pytest.mark.parametrize("algo", ["self", "level", "tiled", "tiled_levels", "chains", "permuted",
-                                  "column"])
+                                  "column", "blocked"])
 @pytest.mark.parametrize("name", list(MATRICES))
 def test_solve_fp64(name, algo):
     A = mat(name)
@@ -120,7 +135,8 @@ def test_solve_fp64(name, algo):
         assert p.status() == (0, -1)
 
 
-@pytest.mark.parametrize("algo", ["self", "level", "tiled", "chains", "permuted", "column"])
+@pytest.mark.parametrize("algo", ["self", "level", "tiled", "chains", "permuted", "column",
+                                  "blocked"])
 @pytest.mark.parametrize("name", ["general", "ilu_L", "ilu_U", "long_rows"])
 def test_solve_fp32(name, algo):
     A = mat(name)
@@ -151,6 +167,7 @@ def test_every_launch_shape(lanes, block):
             for tile in (32, 100, 2048, 6112):
                 p.set_tiling(tile, order)
                 assert relerr(p.solve(bt, algo="tiled"), ref) <= TOL64
+                assert relerr(p.solve(bt, algo="blocked"), ref) <= TOL64
 
 
 @pytest.mark.parametrize("k", [2, 3, 8, 32, 33])
@@ -165,7 +182,8 @@ def test_multi_rhs(k, algo):
             assert relerr(x, ref) <= TOL64
 
 
-@pytest.mark.parametrize("algo", ["self", "level", "tiled", "chains", "permuted", "column"])
+@pytest.mark.parametrize("algo", ["self", "level", "tiled", "chains", "permuted", "column",
+                                  "blocked"])
 def test_leading_dimension_and_in_place(algo):
     A = mat("general")
     k, ld = 3, 5
@@ -187,7 +205,7 @@ def test_leading_dimension_and_in_place(algo):
 
 
 @pytest.mark.parametrize("algo", ["self", "level", "tiled", "tiled_levels", "chains", "permuted",
-                                  "column"])
+                                  "column", "blocked"])
 @pytest.mark.parametrize("name", ["workload0", "ilu_L", "ilu_U", "general", "general_upper",
                                   "long_rows", "unit_nodiag", "bidiag"])
 def test_solve_transpose(name, algo):
@@ -227,9 +245,13 @@ def test_bitwise_determinism_and_algo_agreement():
                 assert torch.equal(p.solve(bt, algo="tiled"), first)
         for _ in range(3):
             assert torch.equal(p.solve(bt, algo="chains"), first)
-        # so does the level-ordered copy, whose rows keep their entry order
+        # so do the level-ordered copy, whose rows keep their entry order, and
+        # the blocked solve on it (any tile size)
         for _ in range(3):
             assert torch.equal(p.solve(bt, algo="permuted"), first)
+        for tile in (64, 1000, 4096):
+            p.set_tiling(tile, False)
+            assert torch.equal(p.solve(bt, algo="blocked"), first)
         tg = torch.tensor(synth.uniform(A.n, 23), device=dev())
         assert torch.equal(p.solve_transpose(tg, algo="permuted"), p.solve_transpose(tg))
         # the column-wise form (Alg. 4) adds contributions atomically in
@@ -334,7 +356,7 @@ def test_bad_rowptr():
     assert ei.value.status == 2
 
 
-@pytest.mark.parametrize("algo", ["self", "tiled", "chains", "permuted", "column"])
+@pytest.mark.parametrize("algo", ["self", "tiled", "chains", "permuted", "column", "blocked"])
 def test_timeout_is_reported_and_solve_finishes(algo):
     """A row that is never published: every row that depends on it gives up
     after the spin limit, records SPTRSV_ERR_TIMEOUT and publishes NaN; rows
@@ -495,5 +517,6 @@ def test_autotuner_picks_an_algorithm_and_stays_exact():
         bt = torch.tensor(b, device=dev())
         res = autotune.tune_algos(p, bt, use_cache=False, lanes=(2, 8), blocks=(256,),
                                   grids=(0, 2), tiles=(512, 2048))
-        assert res["algo"] in ("self", "permuted", "tiled", "chains") and p.best_algo == res["algo"]
+        assert res["algo"] in ("self", "permuted", "blocked", "tiled", "chains")
+        assert p.best_algo == res["algo"]
         assert relerr(p.solve(bt, algo="auto"), ref) <= TOL64
