@@ -167,7 +167,9 @@ __device__ __forceinline__ void kahn_frontier(const int* __restrict__ dptr,
 // most `narrow` rows runs on block 0 alone, which keeps going through
 // consecutive narrow levels separated only by block barriers (no grid-wide
 // step) and then publishes (base, size, level) in ctl[0..2]; the other
-// blocks meanwhile wait at the one grid barrier that closes the run.  Deep,
+// blocks meanwhile wait at the grid barrier that closes the run.  A run
+// opens with one more grid barrier, after which every block has read the
+// size it starts from, so block 0 may clear and reuse that counter.  Deep,
 // narrow dependency graphs thus cost a block barrier per level, not a grid
 // barrier.  cnt[0] holds the roots queued by kahn_roots_k; cnt[1], cnt[2]
 // start at zero.  Writes the level count and cnt[3] = rows leveled.
@@ -199,6 +201,11 @@ __global__ void kahn_persistent_k(const int* __restrict__ dptr, const int* __res
             }
         }
         if (size <= narrow) {
+            // Every block must have read `size` (the counter of the grid
+            // barrier just passed) before block 0 runs ahead: its next levels
+            // clear and reuse that counter.  One extra grid barrier per run.
+            ++gen;
+            if (!grid_barrier(arrivals, gen * gridDim.x, limit, status, level)) return;
             if (blockIdx.x == 0) {
                 // at most kNarrowRun levels per run, so the other blocks' wait
                 // at the closing barrier stays far below its spin limit; a run

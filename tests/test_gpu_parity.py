@@ -94,6 +94,24 @@ def test_automatic_analysis_choice():
             assert_levels_equal(p.levels(transpose=True), A, transpose=True)
 
 
+def test_automatic_analysis_many_plans():
+    """Many plans in a row, as the benchmark's batch comparison makes them:
+    every automatic analysis (Kahn's launch with its narrow runs, or the
+    sweep after the probe) must finish and give the oracle's levels."""
+    sizes = synth.batch_sizes(48, 77, nmin=300, nmax=9000)
+    for s_, nk in enumerate(sizes):
+        A = synth.general_lower(int(nk), 500 + s_)
+        with plan_for(A) as p:
+            assert_levels_equal(p.levels(), A)
+            assert p.status() == (0, -1)
+    for dims in ((40, 7), (3, 500), (9, 9, 9)):    # wide, narrow, and in between
+        A = synth.laplacian_triangles(dims, 9 if len(dims) == 2 else 27)[0]
+        for method in ("auto", "kahn_persistent"):
+            with plan_for(A) as p:
+                p.reanalyze(method)
+                assert_levels_equal(p.levels(), A)
+
+
 @pytest.mark.parametrize("method", ["kahn_host_loop", "kahn_persistent", "sweep", "auto"])
 @pytest.mark.parametrize("name", ["workload0", "ilu_L", "ilu_U", "general", "general_upper",
                                   "bidiag", "diag", "long_rows", "unit_nodiag", "lap3d_27pt"])

@@ -63,3 +63,35 @@ def test_break_even_solve_count():
         k = bench._break_even(sa, ta, sb, tb)
         assert sa + k * ta < sb + k * tb
         assert k == 0 or not (sa + (k - 1) * ta < sb + (k - 1) * tb)
+
+
+class _FakePlan:
+    """Records the tuning calls the autotuner makes (no GPU)."""
+
+    def __init__(self):
+        self.calls = []
+        self.best_algo = "self"
+
+    def set_tuning(self, lanes, block, max_blocks):
+        self.calls.append(("tuning", lanes, block, max_blocks))
+
+    def set_tiling(self, tile_rows, level_order=False):
+        self.calls.append(("tiling", tile_rows, level_order))
+
+
+def test_tune_cache_round_trip():
+    """The benchmark's tune cache stores the autotuner's choice as JSON and
+    re-applies it without timing anything (a profiler run of the same command
+    then uses the plain run's launch shapes)."""
+    import json
+
+    from paper_1710_04985_gb300 import autotune
+    for algo, tiles in (("permuted", False), ("blocked", True), ("tiled", True)):
+        result = {"algo": algo, "best": (2, 128, 608, 0.47, 512, False), "per_algo": {}}
+        ch = json.loads(json.dumps(autotune.choice(result)))
+        assert ch == [algo, 2, 128, 608, 512, False]
+        p = _FakePlan()
+        out = autotune.apply_choice(p, ch)
+        assert p.best_algo == algo and out["algo"] == algo
+        assert p.calls[0] == ("tuning", 2, 128, 608)
+        assert (("tiling", 512, False) in p.calls) == tiles
