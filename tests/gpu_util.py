@@ -5,7 +5,9 @@ import torch
 import oracle
 import synth
 
-# FP64 bar (max|x - x_ref| / max|x_ref|); see the parity notes in the design doc.
+# FP64 bar on max|x - x_ref| / max|x_ref|: the pull form reduces each row in a
+# fixed order that differs from the sequential oracle's only in rounding, and the
+# test matrices are well conditioned, so 1e-12 leaves several digits of margin.
 TOL64 = 1e-12
 # FP32 solves against the FP64 oracle: diagonally dominant / ILU factors keep
 # the forward error within a small multiple of n_row * 2^-24.
