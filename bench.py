@@ -569,7 +569,8 @@ def table2_sweep(args):
                                         lanes=(1, 2, 4, 8, 16), blocks=(256, 512),
                                         grids=(0, 2), reps=3)
                 tb = autotune.tune(p, rhs, out, algo="blocked", lanes=(1, 2, 4, 8),
-                                   blocks=(512, 1024), grids=(0,), tiles=(512, 2048), reps=3)
+                                   blocks=(512, 1024), grids=(0,), tiles=(256, 512, 2048),
+                                   reps=3)
                 if tb["best"][3] < t["best"][3]:
                     t = {"algo": "blocked", "best": tb["best"]}
                 autotune.apply_choice(p, autotune.choice(t))

@@ -78,7 +78,8 @@ def tune(plan, b, x=None, algo="self", lanes=LANES, blocks=BLOCKS, grids=GRID_FR
         return ms
 
     default_block = 256 if 256 in blocks else blocks[0]
-    tile0 = 2048 if 2048 in tiles else tiles[0]
+    # the blocked form prefers small tiles (a tile should hold a few narrow levels)
+    tile0 = min(tiles) if algo == "blocked" else (2048 if 2048 in tiles else tiles[0])
     first_grid = 2 * sms if tiles_used else 0
     orders = tile_orders if algo == "tiled" else (False,)
     for order in orders:
@@ -128,7 +129,7 @@ def tune_algos(plan, b, x=None, algos=("self", "permuted", "blocked", "tiled", "
             # narrow levels: large blocks cover a level or more
             per[a] = tune(plan, b, x, algo=a, reps=reps, use_cache=use_cache,
                           lanes=(1, 2, 4, 8), blocks=(512, 1024), grids=(0,),
-                          tiles=(512, 2048))
+                          tiles=(256, 512, 2048))
         else:
             per[a] = tune(plan, b, x, algo=a, reps=reps, use_cache=use_cache, **kw)
     name = min(per, key=lambda a: per[a]["best"][3])

@@ -43,6 +43,8 @@ MATRICES = {
 
 _cache = {}
 
+ALL_ALGOS = ("self", "level", "permuted", "blocked", "column", "tiled", "chains")
+
 
 def mat(name):
     if name not in _cache:
@@ -287,19 +289,25 @@ def test_empty_matrix():
                        torch.zeros(0, dtype=torch.int32, device=d),
                        torch.zeros(0, dtype=torch.float64, device=d))
     assert p.levels()["nlev"] == 0
-    out = p.solve(torch.zeros(0, dtype=torch.float64, device=d))
-    assert out.numel() == 0
+    for algo in ALL_ALGOS:
+        out = p.solve(torch.zeros(0, dtype=torch.float64, device=d), algo=algo)
+        assert out.numel() == 0
+        assert p.solve_transpose(torch.zeros(0, dtype=torch.float64, device=d),
+                                 algo=algo).numel() == 0
+    p.reanalyze("auto")
     p.close()
 
 
 def test_single_row_and_values_update():
     A = synth.CSR(1, np.array([0, 1], np.int32), np.array([0], np.int32), np.array([4.0]))
     with plan_for(A) as p:
-        for algo in ("self", "level"):
+        for algo in ALL_ALGOS:
             x = p.solve(torch.tensor([2.0], device=dev(), dtype=torch.float64), algo=algo)
-            assert x.item() == 0.5
+            assert x.item() == 0.5, algo
         p.set_values(torch.tensor([8.0], device=dev(), dtype=torch.float64))
-        assert p.solve(torch.tensor([2.0], device=dev(), dtype=torch.float64)).item() == 0.25
+        for algo in ALL_ALGOS:
+            x = p.solve(torch.tensor([2.0], device=dev(), dtype=torch.float64), algo=algo)
+            assert x.item() == 0.25, algo
 
 
 def test_values_change_without_reanalysis():
