@@ -59,11 +59,21 @@ KERNELS = {
 }
 
 
+def _code_only(text):
+    """Source text without comments and with whitespace collapsed, so that a
+    comment edit does not count as a kernel change."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_source_sha(algo="self"):
+    """Hash of the code (not the comments) of a solve kernel's source file and
+    the shared headers: an ncu figure taken on other code is not reused."""
     h = hashlib.sha256()
     for f in (KERNELS[algo][1], "common.cuh", "internal.h"):
-        with open(os.path.join(ROOT, "paper_1710_04985_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1710_04985_gb300", "csrc", f)) as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:12]
 
 

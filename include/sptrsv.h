@@ -158,7 +158,9 @@ typedef enum {
     SPTRSV_ANALYSIS_AUTO = 3              /* what sptrsv_analyze does: the persistent
                                              Kahn launch, which gives up after 256
                                              levels if they hold fewer than 112 rows
-                                             on average (a deep, narrow graph), and
+                                             on average (a deep, narrow graph; if the
+                                             levels are still widening it looks again
+                                             at level 1024 and asks for 168), and
                                              then the sweep                         */
 } sptrsv_analysis_t;
 

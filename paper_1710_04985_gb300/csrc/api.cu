@@ -243,8 +243,9 @@ sptrsv_status_t kahn_levels(sptrsv_plan_t P, const int* ptr, const int* idx, con
         const int narrow = (int)env_ll("SPTRSV_KAHN_NARROW", block / 32);
         // Probe (automatic method only): after 256 levels, fewer than 112
         // rows per level on average means a deep, narrow graph, where a
-        // grid barrier per level loses to the sweep (measured: 2.2-3.1 us
-        // per level against the sweep's 1.2-1.3 us on such graphs).
+        // grid barrier per level loses to the sweep (measured: 2.2-3.6 us
+        // per level against the sweep's 1.2-1.3 us on such graphs); levels
+        // still widening at that point are judged again at level 1024.
         const int probe_level = probe ? 256 : 0;
         e = launch_kahn_persistent(dptr, didx, count, L.lev, queue, qend, ctl, n, narrow,
                                    probe_level, 112, arrivals, nlev_dev, P->status,

@@ -161,7 +161,9 @@ int kahn_persistent_blocks_per_sm(int block);
 // cnt[3] = rows leveled and *nlev_out = levels.  ctl: 3 ints of scratch.
 // Levels of at most `narrow` rows run on block 0 alone.  With probe_level
 // > 0, the launch gives up (*nlev_out = -1) when fewer than
-// probe_level * probe_min_avg rows are leveled after probe_level levels.
+// level * probe_min_avg rows are leveled after probe_level levels, unless
+// the levels are still widening, in which case it looks again (once) at
+// four times that level with a 1.5 times larger average.
 cudaError_t launch_kahn_persistent(const int* dptr, const int* didx, int* count, int* lev,
                                    int* queue, int* cnt, int* ctl, int n, int narrow,
                                    int probe_level, int probe_min_avg,

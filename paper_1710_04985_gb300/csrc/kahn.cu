@@ -188,16 +188,27 @@ __global__ void kahn_persistent_k(const int* __restrict__ dptr, const int* __res
     long long base = 0;
     int size = *(volatile int*)cnt;  // roots, queued before this launch
     int level = 0;
-    bool probed = probe_level <= 0;
+    // Level at which the next probe is taken (0: none left).
+    int next_probe = probe_level > 0 ? probe_level : 0;
+    bool postponed = false;
     while (size > 0) {
         // Early exit for deep, narrow graphs (a grid barrier per level costs
-        // more there than the sweep): every block sees the same (base,
-        // level) here, so all of them decide alike.
-        if (!probed && level >= probe_level) {
-            probed = true;
-            if (base < (long long)level * probe_min_avg) {
-                if (blockIdx.x == 0 && threadIdx.x == 0) *nlev_out = -1;
-                return;
+        // more there than the sweep): every block sees the same (base, size,
+        // level) here, so all of them decide alike.  Levels that are still
+        // widening (the current one at least 1.5 times the average so far)
+        // get one second look at four times the level, which then asks for
+        // a 1.5 times larger average.
+        if (next_probe > 0 && level >= next_probe) {
+            next_probe = 0;
+            const long long need = postponed ? (3ll * probe_min_avg) / 2 : probe_min_avg;
+            if (base < (long long)level * need) {
+                if (!postponed && 2ll * size * level >= 3ll * base) {
+                    postponed = true;
+                    next_probe = 4 * level;
+                } else {
+                    if (blockIdx.x == 0 && threadIdx.x == 0) *nlev_out = -1;
+                    return;
+                }
             }
         }
         if (size <= narrow) {
@@ -211,7 +222,7 @@ __global__ void kahn_persistent_k(const int* __restrict__ dptr, const int* __res
                 // at the closing barrier stays far below its spin limit; a run
                 // also stops at the probe level so that the probe is taken
                 for (int run = 0; run < kNarrowRun && size > 0 && size <= narrow &&
-                                   (probed || level < probe_level);
+                                   (next_probe == 0 || level < next_probe);
                      ++run) {
                     if (threadIdx.x == 0) cnt[(level + 2) % 3] = 0;
                     __syncthreads();

@@ -85,9 +85,14 @@ def test_automatic_analysis_choice():
     """The plan's own setup (SPTRSV_ANALYSIS_AUTO) levels wide graphs with
     Kahn's algorithm in one launch and gives up on deep, narrow ones after
     256 levels, falling back to the sweep; the levels are the same."""
-    for name, want in (("ilu_L", "kahn_persistent"), ("lap3d_27pt", "kahn_persistent"),
-                       ("bidiag", "sweep"), ("bidiag_upper", "sweep")):
-        A = mat(name)
+    widening = synth.laplacian_triangles((300, 300), 9)[0]   # 898 levels, widening slowly
+    narrow = synth.laplacian_triangles((40, 2000), 5)[0]     # 2039 levels of <= 40 rows
+    cases = (("ilu_L", "kahn_persistent"), ("lap3d_27pt", "kahn_persistent"),
+             ("bidiag", "sweep"), ("bidiag_upper", "sweep"),
+             (widening, "kahn_persistent"), (narrow, "sweep"))
+    for name, want in cases:
+        A = mat(name) if isinstance(name, str) else name
+        name = name if isinstance(name, str) else A.name
         with plan_for(A) as p:
             assert p.analysis_method() == want, name
             assert_levels_equal(p.levels(), A)
