@@ -411,6 +411,25 @@ def main():
                                     "graph_solves_per_s": 2e3 / lvg_ms}
         extra["cusparse_spsv"] = cusparse_pair(L, U, pl, pu, b, dev, lv_steps)
         self_ms = ms / args.steps
+        # per-step distribution, back to back and with L2 flushed before every
+        # step (a 2 x L2 memset outside the events)
+        flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
+        dist_steps = {"back_to_back": [], "l2_flushed": []}
+        for mode in dist_steps:
+            for _ in range(50):
+                if mode == "l2_flushed":
+                    flush.zero_()
+                f0 = torch.cuda.Event(enable_timing=True)
+                f1 = torch.cuda.Event(enable_timing=True)
+                f0.record()
+                step()
+                f1.record()
+                f1.synchronize()
+                dist_steps[mode].append(f0.elapsed_time(f1))
+        del flush
+        extra["step_ms_distribution"] = {
+            m: {"median": statistics.median(v), "mean": statistics.fmean(v), "min": min(v),
+                "max": max(v), "steps": len(v)} for m, v in dist_steps.items()}
         # dependency-latency bound: a bidiagonal chain (n = 10^5, every row
         # waits on the previous one) gives the time of one dependency hop
         # t_hop; a solve of nlev levels cannot beat nlev * t_hop
@@ -748,12 +767,12 @@ def extended(dev, args):
     for k in (1, 8, 32):
         bk = torch.tensor(synth.uniform((L.n, k) if k > 1 else L.n, 3000 + k), device=dev)
         xk = torch.empty_like(bk)
-        if k == 1:
-            autotune.tune_algos(pl, bk, xk, reps=2)
+        t = autotune.tune_algos(pl, bk, xk, reps=2)   # k > 1: the multi-RHS width too
         ms = _events_ms(lambda: pl.solve(bk, out=xk, algo="auto"), 5)
         byts = L.nnz * 12 + L.n * 8 + L.n * 16 * k
         mr[f"k{k}"] = {"ms": ms, "rhs_solves_per_s": k * 1e3 / ms,
-                       "effective_gbs": byts / ms / 1e6}
+                       "effective_gbs": byts / ms / 1e6, "algo": t["algo"],
+                       "lanes_per_row": t["best"][0]}
     res["multi_rhs_ilu_L"] = mr
 
     # FP32 bulk + FP64 refinement on the ILU L factor and on the general matrix

@@ -300,11 +300,22 @@ SPTRSV_API sptrsv_status_t sptrsv_refresh_values(sptrsv_plan_t plan, void *strea
  * many as fit on the device at once; the default is 2 blocks per SM, which
  * keeps enough rows waiting ahead of the dependency frontier without
  * flooding L2 with polls).  Applies to the forward and the transposed
- * solves.  Multi-RHS solves pick their own width from nrhs. */
+ * solves.  Multi-RHS solves have their own launch shape
+ * (sptrsv_set_mrhs_tuning), by default this block size and grid cap. */
 SPTRSV_API sptrsv_status_t sptrsv_set_tuning(sptrsv_plan_t plan, int lanes_per_row,
                                   int block_size, int max_blocks);
 SPTRSV_API sptrsv_status_t sptrsv_get_tuning(sptrsv_plan_t plan, int *lanes_per_row,
                                   int *block_size, int *max_blocks);
+
+/* Launch shape of multi-RHS solves (nrhs > 1, Sec. 1's many right-hand
+ * sides), kept apart from the single-RHS one: a group of lanes_per_row lanes
+ * in {4, 8, 16, 32} owns a row, lane l handling columns l, l + lanes_per_row,
+ * ...; every column is folded in entry order, so the width does not change the
+ * results.  lanes_per_row 0 (the default) picks one lane per column up to 16
+ * lanes; block_size 0 and max_blocks -1 (the defaults) use the single-RHS
+ * values of sptrsv_set_tuning. */
+SPTRSV_API sptrsv_status_t sptrsv_set_mrhs_tuning(sptrsv_plan_t plan, int lanes_per_row,
+                                                  int block_size, int max_blocks);
 
 /* Tiles of SPTRSV_ALGO_SELF_TILED: tile_rows consecutive positions of the
  * substitution order (level_order = 0: natural row order, reversed for an

@@ -48,6 +48,7 @@ SIGNATURES = [
     ("sptrsv_refresh_values", _c_int, [_vp, _vp]),
     ("sptrsv_set_tuning", _c_int, [_vp, _c_int, _c_int, _c_int]),
     ("sptrsv_get_tuning", _c_int, [_vp, _ip, _ip, _ip]),
+    ("sptrsv_set_mrhs_tuning", _c_int, [_vp, _c_int, _c_int, _c_int]),
     ("sptrsv_set_spin_limit", _c_int, [_vp, _c_ll]),
     ("sptrsv_set_tiling", _c_int, [_vp, _c_int, _c_int]),
     ("sptrsv_levels", _c_int, [_vp, _c_int, _ip, _pp, _pp, _pp]),

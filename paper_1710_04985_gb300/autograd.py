@@ -12,12 +12,19 @@ import torch
 
 from .solver import TriangularPlan
 
+# Algorithms that solve from the plan's level-ordered copy of the values.
+COPYING_ALGOS = ("permuted", "blocked")
+
 
 class _TriangularSolve(torch.autograd.Function):
     @staticmethod
     def forward(ctx, vals, b, plan, algo, transpose):
         if vals.data_ptr() != plan.vals.data_ptr():
             plan.set_values(vals)
+        elif (plan.best_algo if algo == "auto" else algo) in COPYING_ALGOS:
+            # the level-ordered copy is a snapshot: an in-place update of
+            # `vals` (an optimizer step) keeps the pointer, so refresh it
+            plan.refresh_values()
         x = plan.solve_transpose(b, algo=algo) if transpose else plan.solve(b, algo=algo)
         ctx.plan = plan
         ctx.algo = algo

@@ -55,11 +55,17 @@ def tune(plan, b, x=None, algo="self", lanes=LANES, blocks=BLOCKS, grids=GRID_FR
     Sets the winner on the plan and returns ``{"best": (lanes, block,
     max_blocks, ms, tile_rows, level_order), "table": [...]}``."""
     nrhs = 1 if b.dim() == 1 else b.shape[1]
+    mrhs = nrhs > 1 and algo in ("self", "level")
+    if mrhs:
+        # multi-RHS solves: the width is the multi-RHS one (4..32 lanes); one
+        # lane per column at most
+        cap = max(4, 1 << (nrhs - 1).bit_length())
+        lanes = tuple(w for w in (4, 8, 16, 32) if w <= cap)
     key = signature(plan, nrhs, algo) + (transpose, tuple(lanes), tuple(blocks), tuple(grids),
                                          tuple(tiles), tuple(tile_orders))
     if use_cache and key in _CACHE:
         best = _CACHE[key]["best"]
-        _apply(plan, best, algo)
+        _apply(plan, best, algo, nrhs)
         return _CACHE[key]
     if x is None:
         x = torch.empty_like(b)
@@ -70,7 +76,10 @@ def tune(plan, b, x=None, algo="self", lanes=LANES, blocks=BLOCKS, grids=GRID_FR
     tiles_used = algo in ("tiled", "blocked")
 
     def run(w, blk, mb, tile, order):
-        plan.set_tuning(w, blk, mb)
+        if mrhs:
+            plan.set_mrhs_tuning(w, blk, mb)
+        else:
+            plan.set_tuning(w, blk, mb)
         if tiles_used:
             plan.set_tiling(tile, order)
         ms = time_solve(plan, b, x, algo, reps, transpose)
@@ -97,14 +106,19 @@ def tune(plan, b, x=None, algo="self", lanes=LANES, blocks=BLOCKS, grids=GRID_FR
             if tile != tile0 and tile * esize <= 48 * 1024 - 256:
                 run(bb[0], bb[1], bb[2], tile, bb[5])
     best = min(table, key=lambda r: r[3])
-    _apply(plan, best, algo)
-    result = {"best": best, "table": table}
+    _apply(plan, best, algo, nrhs)
+    result = {"best": best, "table": table, "nrhs": nrhs}
     _CACHE[key] = result
     return result
 
 
-def _apply(plan, best, algo):
-    plan.set_tuning(best[0], best[1], best[2])
+def _apply(plan, best, algo, nrhs=1):
+    """Set a tuning row on the plan: (lanes, block, max_blocks, ms, tile,
+    level_order), lanes being the multi-RHS width when nrhs > 1."""
+    if nrhs > 1 and algo in ("self", "level"):
+        plan.set_mrhs_tuning(best[0], best[1], best[2])
+    else:
+        plan.set_tuning(best[0], best[1], best[2])
     if algo in ("tiled", "blocked"):
         plan.set_tiling(best[4], best[5])
 
@@ -133,8 +147,9 @@ def tune_algos(plan, b, x=None, algos=("self", "permuted", "blocked", "tiled", "
         else:
             per[a] = tune(plan, b, x, algo=a, reps=reps, use_cache=use_cache, **kw)
     name = min(per, key=lambda a: per[a]["best"][3])
-    _apply(plan, per[name]["best"], name)
-    plan.best_algo = name
+    _apply(plan, per[name]["best"], name, nrhs)
+    if nrhs == 1:  # multi-RHS solves always run the in-place kernel
+        plan.best_algo = name
     return {"algo": name, "best": per[name]["best"], "per_algo": per}
 
 

@@ -224,6 +224,13 @@ class TriangularPlan:
         check(_lib.load().sptrsv_set_tuning(self._h, lanes_per_row, block_size, max_blocks),
               "sptrsv_set_tuning")
 
+    def set_mrhs_tuning(self, lanes_per_row=0, block_size=0, max_blocks=-1):
+        """Launch shape of multi-RHS solves: width (0: one lane per column up
+        to 16), block size (0) and grid cap (-1) default to the single-RHS
+        ones."""
+        check(_lib.load().sptrsv_set_mrhs_tuning(self._h, int(lanes_per_row), int(block_size),
+                                                 int(max_blocks)), "sptrsv_set_mrhs_tuning")
+
     @property
     def tuning(self):
         a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()

@@ -207,6 +207,38 @@ def test_multi_rhs(k, algo):
             assert relerr(x, ref) <= TOL64
 
 
+def test_multi_rhs_width_does_not_change_results():
+    """Every column is folded in entry order by one lane, so the multi-RHS
+    width (lanes per row, several columns per lane when narrower than k)
+    changes the schedule only: results are bitwise equal and exact."""
+    from paper_1710_04985_gb300 import autotune
+    A = mat("general")
+    for k in (5, 33):
+        b = synth.uniform((A.n, k), 40 + k)
+        ref = oracle.solve(A.rowptr, A.colidx, A.vals, b)
+        with plan_for(A) as p:
+            bt = torch.tensor(b, device=dev())
+            first = p.solve(bt).clone()
+            assert relerr(first, ref) <= TOL64
+            for w in (4, 8, 16, 32, 0):
+                p.set_mrhs_tuning(w, 128 if w == 8 else 0, 76 if w == 16 else -1)
+                assert torch.equal(p.solve(bt), first), (k, w)
+                # the level-scheduled form uses the same width (and divides by
+                # d(i) where the self-scheduled one multiplies by 1/d(i))
+                assert relerr(p.solve(bt, algo="level"), ref) <= TOL64
+            res = autotune.tune_algos(p, bt, use_cache=False, blocks=(256,), grids=(0, 2))
+            assert res["best"][0] in (4, 8, 16, 32)
+            assert torch.equal(p.solve(bt, algo="auto"), first)
+    with plan_for(A) as p:
+        from paper_1710_04985_gb300 import SptrsvError
+        before = p.tuning
+        for bad in ((3, 0, -1), (8, 48, -1), (8, 0, -2)):
+            with pytest.raises(SptrsvError):
+                p.set_mrhs_tuning(*bad)
+        p.set_mrhs_tuning(16, 512, 4)
+        assert p.tuning == before          # the single-RHS shape is left alone
+
+
 @pytest.mark.parametrize("algo", ["self", "level", "tiled", "chains", "permuted", "column",
                                   "blocked"])
 def test_leading_dimension_and_in_place(algo):
@@ -325,6 +357,24 @@ def test_values_change_without_reanalysis():
         p.vals.mul_(2.0)
         ref = oracle.solve(A.rowptr, A.colidx, 2.0 * A.vals, b)
         assert relerr(p.solve(bt), ref) <= TOL64
+
+
+def test_autograd_sees_in_place_value_updates_with_copying_algorithms():
+    """An optimizer step updates the values tensor in place; the autograd path
+    must not solve from a stale level-ordered copy."""
+    from paper_1710_04985_gb300 import sparse_triangular_solve
+    A = mat("ilu_L")
+    b = synth.uniform(A.n, 26)
+    with plan_for(A) as p:
+        v = p.vals
+        bt = torch.tensor(b, device=dev())
+        for algo in ("permuted", "blocked"):
+            sparse_triangular_solve(p, v, bt, algo=algo)
+            with torch.no_grad():
+                v.mul_(0.5)
+            x = sparse_triangular_solve(p, v, bt, algo=algo)
+            ref = oracle.solve(A.rowptr, A.colidx, v.cpu().numpy(), b, unit=A.unit)
+            assert relerr(x.detach(), ref) <= TOL64, algo
 
 
 def test_level_ordered_copy_follows_value_updates():
