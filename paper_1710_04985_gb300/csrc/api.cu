@@ -241,7 +241,8 @@ sptrsv_status_t kahn_levels(sptrsv_plan_t P, const int* ptr, const int* idx, con
         // One block of 1024 threads per SM keeps the grid barrier short (one
         // arrival per SM); a level with at most one row per warp of a block
         // runs on block 0 alone.
-        const int block = (int)env_ll("SPTRSV_KAHN_BLOCK", 1024);
+        int block = (int)env_ll("SPTRSV_KAHN_BLOCK", 1024);
+        if (block < 64 || block > 1024 || block % 32 != 0) block = 1024;
         long long per_sm = env_ll("SPTRSV_KAHN_BLOCKS_PER_SM", 1);
         const long long fit = kahn_persistent_blocks_per_sm(block);
         if (per_sm > fit) per_sm = fit;
