@@ -56,6 +56,9 @@ KERNELS = {
     "tiled": ("tiled_solve_k1", "solve_tiled.cu", "tiled_solve_k1_ilu0_7pt_128.md"),
     "chains": ("chain_solve_k1", "solve_chain.cu", "chain_solve_k1_ilu0_7pt_128.md"),
     "permuted": ("self_solve_k1", "solve_self.cu", "self_solve_k1_permuted_ilu0_7pt_128.md"),
+    "blocked": ("blocked_solve_k1", "solve_blocked.cu", "blocked_solve_k1_ilu0_7pt_128.md"),
+    "partitioned": ("blocked_solve_k1", "solve_blocked.cu",
+                    "blocked_solve_k1_partitioned_ilu0_7pt_128.md"),
 }
 
 
@@ -211,8 +214,11 @@ def main():
     ap.add_argument("--lanes", type=int, default=4)
     ap.add_argument("--max-blocks", type=int, default=304)
     ap.add_argument("--algo", default="self",
-                    choices=["self", "level", "tiled", "chains", "permuted", "column"])
+                    choices=["self", "level", "tiled", "chains", "permuted", "column",
+                             "blocked", "partitioned"])
     ap.add_argument("--block", type=int, default=256)
+    ap.add_argument("--part-rows", type=int, default=0,
+                    help="--single-solve: rows per part of the partitioned form (0: automatic)")
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--extended", action="store_true",
                     help="also measure the general, multi-RHS, batched, refined and autograd "
@@ -495,7 +501,13 @@ def main():
                                 "chains": "self-scheduled over segments of consecutive "
                                           "rows, in-segment values passed by shuffle",
                                 "permuted": "self-scheduled in level order on a level-ordered "
-                                            "copy of the matrix (Sec. 4.3 remark 2)"},
+                                            "copy of the matrix (Sec. 4.3 remark 2)",
+                                "blocked": "self-scheduled, a thread block per tile of the "
+                                           "level-ordered copy, in-tile values in shared "
+                                           "memory",
+                                "partitioned": "self-scheduled, a thread block per part of "
+                                               "consecutive rows (by level inside the part), "
+                                               "in-part values in shared memory"},
                        "tuning": {"L": _tuning_row(tune_l), "U": _tuning_row(tune_u),
                                   "fields": ["lanes_per_row", "block", "max_blocks",
                                              "tile_rows", "tile_level_order"]},
@@ -550,6 +562,7 @@ def single_solve(args):
     p = TriangularPlan(torch.tensor(A.rowptr, device=dev), torch.tensor(A.colidx, device=dev),
                        torch.tensor(A.vals, device=dev), upper=A.upper, unit=A.unit)
     p.set_tuning(args.lanes, args.block, args.max_blocks)
+    p.set_partition(args.part_rows)
     b = torch.tensor(bh, device=dev)
     x = torch.empty_like(b)
     for _ in range(args.repeat):
@@ -558,6 +571,7 @@ def single_solve(args):
     err = float(np.max(np.abs(x.cpu().numpy() - xt)) / np.max(np.abs(xt)))
     print(json.dumps({"single_solve": args.single_solve, "algo": args.algo, "lanes": args.lanes,
                       "block": args.block, "max_blocks": args.max_blocks,
+                      "part_rows": p.partition,
                       "max_rel_err_vs_xtrue": err}))
 
 
@@ -602,6 +616,11 @@ def table2_sweep(args):
                                    reps=3)
                 if tb["best"][3] < t["best"][3]:
                     t = {"algo": "blocked", "best": tb["best"]}
+                tp = autotune.tune(p, rhs, out, algo="partitioned", lanes=(1, 2, 4),
+                                   blocks=(128, 256, 512), grids=(0,), tiles=autotune.PARTS,
+                                   reps=3)
+                if tp["best"][3] < t["best"][3]:
+                    t = {"algo": "partitioned", "best": tp["best"]}
                 autotune.apply_choice(p, autotune.choice(t))
                 return t
 

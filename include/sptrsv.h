@@ -37,7 +37,8 @@
  *  sptrsv_free.  Values may change between solves without re-analysis (the
  *  ILU refactorisation case of Sec. 1); the plan's copies of the values (the
  *  FP32 copy of the refined solve, the level-ordered copy of
- *  SPTRSV_ALGO_SELF_PERMUTED) are brought up to date by
+ *  SPTRSV_ALGO_SELF_PERMUTED and the part-ordered copy of
+ *  SPTRSV_ALGO_SELF_PARTITIONED) are brought up to date by
  *  sptrsv_refresh_values.  The plan OWNS its level arrays, the
  *  transposed pattern, its counters, its status word and its scratch.
  *  Solves on one plan must be serialised (one stream at a time): they share
@@ -140,7 +141,24 @@ typedef enum {
                                      tile's rows are prefetched into L2.  For narrow
                                      levels.  Bitwise equal to SPTRSV_ALGO_SELF for
                                      equal lanes.  One right-hand side; more columns
-                                     fall back to SPTRSV_ALGO_SELF                       */
+                                     fall back to SPTRSV_ALGO_SELF                       */,
+    SPTRSV_ALGO_SELF_PARTITIONED = 7  /* the blocked solve of SPTRSV_ALGO_SELF_BLOCKED
+                                     on a part-ordered copy: the rows are cut into
+                                     parts of part_rows consecutive rows in order of
+                                     substitution (sptrsv_set_partition), listed part
+                                     after part and by level (Sec. 4.1) inside a part,
+                                     and a thread block takes one part per tile, so a
+                                     dependency inside the part passes through shared
+                                     memory and only dependencies on earlier parts
+                                     wait on published values in L2 (Alg. 3).  On a
+                                     grid in natural order a part is a slab of grid
+                                     lines.  Built on first use (a copy of the pattern
+                                     and values, same value snapshot as
+                                     SPTRSV_ALGO_SELF_PERMUTED, allocates and
+                                     synchronises; not during graph capture) and again
+                                     when the part size changes.  Bitwise equal to
+                                     SPTRSV_ALGO_SELF for equal lanes.  One right-hand
+                                     side; more columns fall back to SPTRSV_ALGO_SELF   */
 } sptrsv_algo_t;
 
 /* Level-analysis methods (sptrsv_reanalyze).  All give the same levels and
@@ -325,6 +343,18 @@ SPTRSV_API sptrsv_status_t sptrsv_set_mrhs_tuning(sptrsv_plan_t plan, int lanes_
  * FP64, 12224 in FP32).  Default 2048 rows, substitution order. */
 SPTRSV_API sptrsv_status_t sptrsv_set_tiling(sptrsv_plan_t plan, int tile_rows,
                                              int level_order);
+
+/* Rows per part of SPTRSV_ALGO_SELF_PARTITIONED (0: automatic, the rows
+ * divided evenly over the GPU's SMs).  A part's unknowns must fit one thread
+ * block's shared memory: larger values are reduced to the largest part that
+ * fits (29,024 rows in FP64 and 58,048 in FP32 with 227 KB per block).  The
+ * part-ordered copy is rebuilt on the next partitioned solve.  part_rows < 0
+ * is SPTRSV_ERR_INVALID_ARG. */
+SPTRSV_API sptrsv_status_t sptrsv_set_partition(sptrsv_plan_t plan, int part_rows);
+
+/* The part size the next partitioned solve uses (after the automatic choice
+ * and the shared-memory limit). */
+SPTRSV_API sptrsv_status_t sptrsv_get_partition(sptrsv_plan_t plan, int *part_rows);
 
 /* Upper bound on the polling rounds of one dependency wait before the wait
  * gives up, records SPTRSV_ERR_TIMEOUT with its row and goes on with NaN so

@@ -26,7 +26,7 @@ F64, F32 = 0, 1
 LOWER, UPPER = 0, 1
 NON_UNIT, UNIT = 0, 1
 (ALGO_LEVEL, ALGO_SELF, ALGO_SELF_TILED, ALGO_SELF_CHAINS, ALGO_SELF_PERMUTED,
- ALGO_SELF_COLUMN, ALGO_SELF_BLOCKED) = 0, 1, 2, 3, 4, 5, 6
+ ALGO_SELF_COLUMN, ALGO_SELF_BLOCKED, ALGO_SELF_PARTITIONED) = 0, 1, 2, 3, 4, 5, 6, 7
 
 # (name, restype, argtypes) for every entry point of include/sptrsv.h
 _c_int, _c_ll, _c_dbl = ctypes.c_int, ctypes.c_longlong, ctypes.c_double
@@ -51,6 +51,8 @@ SIGNATURES = [
     ("sptrsv_set_mrhs_tuning", _c_int, [_vp, _c_int, _c_int, _c_int]),
     ("sptrsv_set_spin_limit", _c_int, [_vp, _c_ll]),
     ("sptrsv_set_tiling", _c_int, [_vp, _c_int, _c_int]),
+    ("sptrsv_set_partition", _c_int, [_vp, _c_int]),
+    ("sptrsv_get_partition", _c_int, [_vp, _ip]),
     ("sptrsv_levels", _c_int, [_vp, _c_int, _ip, _pp, _pp, _pp]),
     ("sptrsv_transpose_pattern", _c_int, [_vp, _pp, _pp, _pp]),
     ("sptrsv_status", _c_int, [_vp, _vp, _ip]),

@@ -13,7 +13,7 @@ import torch
 from .solver import TriangularPlan
 
 # Algorithms that solve from the plan's level-ordered copy of the values.
-COPYING_ALGOS = ("permuted", "blocked")
+COPYING_ALGOS = ("permuted", "blocked", "partitioned")
 
 
 class _TriangularSolve(torch.autograd.Function):

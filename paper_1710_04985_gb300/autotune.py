@@ -6,9 +6,10 @@ sub-warp width (lanes per row, hence rows per warp = 32 / lanes) at the
 default block size, then, for that width, the block size and the cap on the
 persistent grid (how many warps wait ahead of the dependency frontier: more
 hides latency, fewer polls less L2 traffic), and for the tiled form the tile
-size.  ``tune_algos`` runs ``tune`` for the level-ordered (in place, on the
-level-ordered copy, and blocked on that copy), tiled and chained
-self-scheduled forms and keeps the fastest, recording it on the plan.
+size (for the partitioned form the part size).  ``tune_algos`` runs
+``tune`` for the level-ordered (in place, on the level-ordered copy, and
+blocked on that copy), partitioned, tiled and chained self-scheduled forms
+and keeps the fastest, recording it on the plan.
 Results are cached per matrix signature for the process.
 """
 from __future__ import annotations
@@ -23,6 +24,8 @@ LANES = (1, 2, 4, 8, 16, 32)
 BLOCKS = (128, 256, 512)
 GRID_FRACTIONS = (0, 4, 2, 1)      # max_blocks = fraction * SMs (0: as many as fit)
 TILES = (1024, 2048, 4096)
+PARTS = (0, 4096, 8192, 16384)     # rows per part of the partitioned form (0: automatic)
+TILED = ("tiled", "blocked", "partitioned")   # forms with a tile (or part) size
 TILE_ORDERS = (False, True)      # substitution order, level order
 
 
@@ -73,14 +76,16 @@ def tune(plan, b, x=None, algo="self", lanes=LANES, blocks=BLOCKS, grids=GRID_FR
     esize = 8 if plan.dtype == torch.float64 else 4
     table = []
 
-    tiles_used = algo in ("tiled", "blocked")
+    tiles_used = algo in TILED
 
     def run(w, blk, mb, tile, order):
         if mrhs:
             plan.set_mrhs_tuning(w, blk, mb)
         else:
             plan.set_tuning(w, blk, mb)
-        if tiles_used:
+        if algo == "partitioned":
+            plan.set_partition(tile)
+        elif tiles_used:
             plan.set_tiling(tile, order)
         ms = time_solve(plan, b, x, algo, reps, transpose)
         table.append((w, blk, mb, ms, tile, order))
@@ -88,14 +93,15 @@ def tune(plan, b, x=None, algo="self", lanes=LANES, blocks=BLOCKS, grids=GRID_FR
 
     default_block = 256 if 256 in blocks else blocks[0]
     # the blocked form prefers small tiles (a tile should hold a few narrow levels)
-    tile0 = min(tiles) if algo == "blocked" else (2048 if 2048 in tiles else tiles[0])
-    first_grid = 2 * sms if tiles_used else 0
+    tile0 = min(tiles) if algo in ("blocked", "partitioned") else (2048 if 2048 in tiles
+                                                                   else tiles[0])
+    first_grid = 2 * sms if algo in ("tiled", "blocked") else 0
     orders = tile_orders if algo == "tiled" else (False,)
     for order in orders:
         for w in lanes:
             run(w, default_block, first_grid, tile0, order)
     w_best, order_best = min(table, key=lambda r: r[3])[0], min(table, key=lambda r: r[3])[5]
-    if algo in ("self", "tiled", "chains", "permuted", "blocked"):
+    if algo in ("self", "tiled", "chains", "permuted", "blocked", "partitioned"):
         for blk in blocks:
             for frac in grids:
                 if (blk, frac * sms) != (default_block, first_grid):
@@ -103,7 +109,8 @@ def tune(plan, b, x=None, algo="self", lanes=LANES, blocks=BLOCKS, grids=GRID_FR
     if tiles_used:
         bb = min(table, key=lambda r: r[3])
         for tile in tiles:
-            if tile != tile0 and tile * esize <= 48 * 1024 - 256:
+            # parts are reduced to what fits shared memory by the library
+            if tile != tile0 and (algo == "partitioned" or tile * esize <= 48 * 1024 - 256):
                 run(bb[0], bb[1], bb[2], tile, bb[5])
     best = min(table, key=lambda r: r[3])
     _apply(plan, best, algo, nrhs)
@@ -119,20 +126,22 @@ def _apply(plan, best, algo, nrhs=1):
         plan.set_mrhs_tuning(best[0], best[1], best[2])
     else:
         plan.set_tuning(best[0], best[1], best[2])
-    if algo in ("tiled", "blocked"):
+    if algo == "partitioned":
+        plan.set_partition(best[4])
+    elif algo in ("tiled", "blocked"):
         plan.set_tiling(best[4], best[5])
 
 
-def tune_algos(plan, b, x=None, algos=("self", "permuted", "blocked", "tiled", "chains"), reps=3,
-               use_cache=True, **kw):
+def tune_algos(plan, b, x=None, algos=("self", "permuted", "blocked", "partitioned", "tiled",
+                                        "chains"), reps=3, use_cache=True, **kw):
     """Tune each self-scheduled form and keep the faster one.
 
     Returns ``{"algo": name, "best": ..., "per_algo": {name: tune(...)}}`` and
     sets ``plan.best_algo`` (used by ``plan.solve(..., algo="auto")``)."""
     nrhs = 1 if b.dim() == 1 else b.shape[1]
     if nrhs > 1:
-        algos = tuple(a for a in algos
-                      if a not in ("tiled", "chains", "permuted", "blocked")) or ("self",)
+        algos = tuple(a for a in algos if a not in
+                      ("tiled", "chains", "permuted", "blocked", "partitioned")) or ("self",)
     per = {}
     for a in algos:
         if a == "tiled" and not kw:
@@ -144,6 +153,11 @@ def tune_algos(plan, b, x=None, algos=("self", "permuted", "blocked", "tiled", "
             per[a] = tune(plan, b, x, algo=a, reps=reps, use_cache=use_cache,
                           lanes=(1, 2, 4, 8), blocks=(512, 1024), grids=(0,),
                           tiles=(256, 512, 2048))
+        elif a == "partitioned" and not kw:
+            # parts of whole grid lines or planes; few lanes (short rows wait on
+            # shared memory)
+            per[a] = tune(plan, b, x, algo=a, reps=reps, use_cache=use_cache,
+                          lanes=(1, 2, 4), blocks=(128, 256, 512), grids=(0,), tiles=PARTS)
         else:
             per[a] = tune(plan, b, x, algo=a, reps=reps, use_cache=use_cache, **kw)
     name = min(per, key=lambda a: per[a]["best"][3])

@@ -57,7 +57,31 @@ struct Levels {
     int* count0 = nullptr;
     int* count = nullptr;
     int method = SPTRSV_ANALYSIS_SWEEP;  // the analysis that produced these levels
+    // Part-ordered copy (SPTRSV_ALGO_SELF_PARTITIONED, built on first use and
+    // again when the part size changes): position k holds row qord[k], rows
+    // in parts of qS consecutive rows, by level inside a part; columns
+    // renumbered to positions (qipos); xq is the publication buffer of its
+    // solves (position order).
+    int qS = 0;
+    int* qord = nullptr;
+    int* qipos = nullptr;
+    int* qptr = nullptr;
+    int* qidx = nullptr;
+    void* qvals = nullptr;
+    void* xq = nullptr;
 };
+
+void free_parts(Levels& L) {
+    cudaFree(L.qord);
+    cudaFree(L.qipos);
+    cudaFree(L.qptr);
+    cudaFree(L.qidx);
+    cudaFree(L.qvals);
+    cudaFree(L.xq);
+    L.qord = L.qipos = L.qptr = L.qidx = nullptr;
+    L.qvals = L.xq = nullptr;
+    L.qS = 0;
+}
 
 struct DeviceGuard {
     int prev = -1;
@@ -146,6 +170,8 @@ struct sptrsv_plan_s {
     int mrhs_lanes = 0, mrhs_block = 0, mrhs_max_blocks = -1;
     int tile_rows = 2048;
     bool tile_level_order = false;
+    int part_rows = 0;   // partitioned solve: rows per part (0: automatic)
+    int smem_optin = 0;  // shared memory a block may opt in to
     SpinPolicy spin{1ll << 24, 256, 128};
     int withhold = -1;
     double analysis_ms = 0.0;
@@ -169,6 +195,7 @@ void free_levels(Levels& L) {
     cudaFree(L.xp);
     cudaFree(L.count0);
     cudaFree(L.count);
+    free_parts(L);
     L = Levels();
 }
 
@@ -622,7 +649,110 @@ cudaError_t refresh_permuted(sptrsv_plan_t P, cudaStream_t s) {
                                             P->num_sms * 16, s);
         if (e != cudaSuccess) return e;
     }
+    for (int d = 0; d < 2; ++d) {
+        Levels& L = d ? P->trn : P->fwd;
+        if (!L.qvals) continue;
+        cudaError_t e = launch_permute_rows(P->f64, P->n, d ? P->tptr : P->rowptr,
+                                            d ? P->tidx : P->colidx, d ? P->tmap : nullptr,
+                                            P->vals, L.qord, L.qipos, L.qptr, nullptr, L.qvals,
+                                            P->num_sms * 16, s);
+        if (e != cudaSuccess) return e;
+    }
     return cudaSuccess;
+}
+
+// Largest part whose unknowns fit a block's shared memory (the blocked
+// kernel keeps a tile's unknowns there).
+int max_part_rows(sptrsv_plan_t P) {
+    const int esize = P->f64 ? 8 : 4;
+    const int room = P->smem_optin - 128;
+    return room > esize * 32 ? (room / esize) & ~31 : 32;
+}
+
+// The part size of the next partitioned solve: the plan's setting or the
+// rows divided evenly over the SMs, at most max_part_rows.
+int resolve_part_rows(sptrsv_plan_t P) {
+    long long S = P->part_rows > 0 ? P->part_rows
+                                   : ((long long)P->n + P->num_sms - 1) / P->num_sms;
+    const int cap = max_part_rows(P);
+    if (S > cap) S = cap;
+    if (S < 1) S = 1;
+    return (int)S;
+}
+
+// Part-ordered copy of one direction's pattern and values for the
+// partitioned solve: the level order jlev stably re-sorted by part, its
+// inverse, the copy with columns renumbered to positions, its self-check
+// (every entry names its own or an earlier position) and the publication
+// buffer.  Allocates and synchronises s.
+sptrsv_status_t build_parts(sptrsv_plan_t P, bool trans, cudaStream_t s) {
+    Levels& L = trans ? P->trn : P->fwd;
+    const int S = resolve_part_rows(P);
+    if (L.qord && L.qS == S) return SPTRSV_OK;
+    if (capturing(s)) return SPTRSV_ERR_NOT_SUPPORTED;
+    CK(cudaStreamSynchronize(s));
+    free_parts(L);
+    const int n = P->n, nnz = P->nnz;
+    const bool upper = trans ? !P->upper : P->upper;
+    const size_t esize = P->f64 ? sizeof(double) : sizeof(float);
+    const int* ptr = trans ? P->tptr : P->rowptr;
+    const int* idx = trans ? P->tidx : P->colidx;
+    const int* vmap = trans ? P->tmap : nullptr;
+    const int nparts = (int)(((long long)n + S - 1) / S);
+    const size_t nz = nnz > 0 ? (size_t)nnz : 1;
+    const int hist_n = radix_hist_entries(n);
+    int *qord = nullptr, *qipos = nullptr, *qptr = nullptr, *qidx = nullptr, *scratch = nullptr;
+    void *qvals = nullptr, *xq = nullptr;
+    cudaError_t e = cudaMalloc(&qord, sizeof(int) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&qipos, sizeof(int) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&qptr, sizeof(int) * ((size_t)n + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&qidx, sizeof(int) * nz);
+    if (e == cudaSuccess) e = cudaMalloc(&qvals, esize * nz);
+    if (e == cudaSuccess) e = cudaMalloc(&xq, esize * (size_t)n);
+    // scratch: key, lens | radix sort: 4 n + 2 hist
+    if (e == cudaSuccess)
+        e = cudaMalloc(&scratch, sizeof(int) * (6 * (size_t)n + 2 * (size_t)hist_n));
+    int* key = scratch;
+    int* lens = key + n;
+    int* k_a = lens + n;
+    int* v_a = k_a + n;
+    int* k_b = v_a + n;
+    int* v_b = k_b + n;
+    int* hist = v_b + n;
+    int* hist_scan = hist + hist_n;
+    if (e == cudaSuccess) e = launch_part_keys(n, L.jlev, S, upper, key, s);
+    if (e == cudaSuccess)
+        e = radix_sort_values(key, L.jlev, n, bits_for(nparts - 1), qord, k_a, v_a, k_b, v_b,
+                              hist, hist_scan, P->status, s);
+    if (e == cudaSuccess) e = launch_inverse_perm(qord, n, qipos, s);
+    if (e == cudaSuccess) e = launch_ordered_lengths(n, ptr, qord, lens, s);
+    if (e == cudaSuccess) e = launch_exclusive_scan(lens, qptr, n, s);
+    if (e == cudaSuccess)
+        e = launch_permute_rows(P->f64, n, ptr, idx, vmap, P->vals, qord, qipos, qptr, qidx,
+                                qvals, P->num_sms * 16, s);
+    if (e == cudaSuccess) e = launch_verify_permuted(n, qptr, qidx, P->status, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    sptrsv_status_t rc = e == cudaSuccess ? SPTRSV_OK : cuda_fail(e);
+    int row = -1;
+    if (rc == SPTRSV_OK && take_status(P, s, &row) != SPTRSV_OK) rc = SPTRSV_ERR_INTERNAL;
+    cudaFree(scratch);
+    if (rc != SPTRSV_OK) {
+        cudaFree(qord);
+        cudaFree(qipos);
+        cudaFree(qptr);
+        cudaFree(qidx);
+        cudaFree(qvals);
+        cudaFree(xq);
+        return rc;
+    }
+    L.qS = S;
+    L.qord = qord;
+    L.qipos = qipos;
+    L.qptr = qptr;
+    L.qidx = qidx;
+    L.qvals = qvals;
+    L.xq = xq;
+    return SPTRSV_OK;
 }
 
 sptrsv_status_t ensure_bytes(void** buf, size_t* have, size_t want, cudaStream_t s) {
@@ -675,6 +805,8 @@ sptrsv_status_t run_solve(sptrsv_plan_t P, bool trans, bool f64, const void* val
     if (permuted) ST(build_permuted(P, trans, s));
     const bool column = algo == SPTRSV_ALGO_SELF_COLUMN && !mrhs;
     if (column) ST(build_column(P, trans, s));
+    const bool parts = algo == SPTRSV_ALGO_SELF_PARTITIONED && !mrhs && f64 == P->f64;
+    if (parts) ST(build_parts(P, trans, s));
     const Levels& L = trans ? P->trn : P->fwd;
     SolveParams p;
     memset(&p, 0, sizeof(p));
@@ -729,6 +861,27 @@ sptrsv_status_t run_solve(sptrsv_plan_t P, bool trans, bool f64, const void* val
         if (grid < 1) grid = 1;
         ST(prof_begin(P, s));
         CK(launch_column_k1(f64, lanes, p, c, (int)grid, block, s));
+        ST(prof_end(P, s));
+        launches = 2;
+    } else if (parts) {
+        // The blocked kernel on the part-ordered copy, one part per tile.
+        // Rows publish to L.xq and store x(i) for the caller; b(i) is read
+        // once, by row i, before x(i) is written, so in place needs no copy.
+        p.ptr = L.qptr;
+        p.idx = L.qidx;
+        p.vmap = nullptr;
+        p.vals = L.qvals;
+        p.xp = L.xq;
+        p.jlev = L.qord;
+        CK(launch_prep_self(f64, P->n, 1, L.xq, 1, nullptr, 0, nullptr, P->counters,
+                            P->num_sms * 8, s));
+        const long long tiles = ((long long)P->n + L.qS - 1) / L.qS;
+        long long grid = (long long)blocked_blocks_per_sm(f64, lanes, block, L.qS) * P->num_sms;
+        if (max_blocks > 0 && grid > max_blocks) grid = max_blocks;
+        if (grid > tiles) grid = tiles;
+        if (grid < 1) grid = 1;
+        ST(prof_begin(P, s));
+        CK(launch_blocked_k1(f64, lanes, p, L.qS, (int)grid, block, s));
         ST(prof_end(P, s));
         launches = 2;
     } else if (permuted) {
@@ -821,7 +974,8 @@ sptrsv_status_t solve_common(sptrsv_plan_t P, bool trans, const void* b, void* x
     if (!P || nrhs < 1 || ld < nrhs ||
         (algo != SPTRSV_ALGO_LEVEL && algo != SPTRSV_ALGO_SELF && algo != SPTRSV_ALGO_SELF_TILED &&
          algo != SPTRSV_ALGO_SELF_CHAINS && algo != SPTRSV_ALGO_SELF_PERMUTED &&
-         algo != SPTRSV_ALGO_SELF_COLUMN && algo != SPTRSV_ALGO_SELF_BLOCKED))
+         algo != SPTRSV_ALGO_SELF_COLUMN && algo != SPTRSV_ALGO_SELF_BLOCKED &&
+         algo != SPTRSV_ALGO_SELF_PARTITIONED))
         return SPTRSV_ERR_INVALID_ARG;
     P->last_launches = 0;
     if (P->n == 0) return SPTRSV_OK;
@@ -858,6 +1012,9 @@ sptrsv_status_t sptrsv_analyze(int n, int nnz, const int* d_rowptr, const int* d
     cudaError_t e = cudaGetDevice(&P->device);
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&P->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
+                                   P->device);
     if (e != cudaSuccess) {
         destroy(P);
         return cuda_fail(e);
@@ -1147,6 +1304,18 @@ sptrsv_status_t sptrsv_set_tiling(sptrsv_plan_t plan, int tile_rows, int level_o
     if (esize * (size_t)tile_rows > 48 * 1024 - 256) return SPTRSV_ERR_INVALID_ARG;
     plan->tile_rows = tile_rows;
     plan->tile_level_order = level_order != 0;
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t sptrsv_set_partition(sptrsv_plan_t plan, int part_rows) {
+    if (!plan || part_rows < 0) return SPTRSV_ERR_INVALID_ARG;
+    plan->part_rows = part_rows;
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t sptrsv_get_partition(sptrsv_plan_t plan, int* part_rows) {
+    if (!plan || !part_rows) return SPTRSV_ERR_INVALID_ARG;
+    *part_rows = resolve_part_rows(plan);
     return SPTRSV_OK;
 }
 

@@ -80,14 +80,21 @@ cudaError_t launch_prep_column(bool f64, const SolveParams& p, const ColumnParam
 cudaError_t launch_column_k1(bool f64, int lanes, const SolveParams& p, const ColumnParams& c,
                              int grid, int block, cudaStream_t s);
 int column_blocks_per_sm(bool f64, int lanes, bool cmap, int block);
-// Blocked self-scheduled solve on the level-ordered copy (solve_blocked.cu):
-// a block per tile of tile_rows consecutive positions, in-tile dependencies
-// through shared memory (tile_rows * element size <= 48 KB - 256 B).
+// Blocked self-scheduled solve on the level- or part-ordered copy
+// (solve_blocked.cu): a block per tile of tile_rows consecutive positions,
+// in-tile dependencies through shared memory (tile_rows * element size at
+// most the device's opt-in shared memory per block, minus 64 B).
 cudaError_t launch_blocked_k1(bool f64, int lanes, const SolveParams& p, int tile_rows, int grid,
                               int block, cudaStream_t s);
 int blocked_blocks_per_sm(bool f64, int lanes, int block, int tile_rows);
 // Resident blocks per SM of the level-ordered-copy form of self_solve_k1.
 int self_perm_blocks_per_sm(bool f64, int lanes, int block);
+
+// ---- partitioned solve (solve_parts.cu): key[k] = part of row jlev[k], parts
+// of S consecutive rows in order of substitution (ascending rows for a lower
+// system, descending for an upper one).
+cudaError_t launch_part_keys(int n, const int* jlev, int S, bool upper, int* key,
+                             cudaStream_t s);
 
 // ---- level-ordered copy (permute.cu)
 // lens[k] = length of row jlev[k].

@@ -213,10 +213,32 @@ __global__ void __launch_bounds__(1024) blocked_solve_k1(SolveParams p, int tile
     }
 }
 
+// Lets blocked_solve_k1<T, W> take the device's opt-in shared memory (tiles
+// beyond 48 KB; once per device).
+template <typename T, int W>
+static cudaError_t blocked_smem_attr() {
+    static unsigned long long done = 0;  // one bit per device
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done & bit) return cudaSuccess;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(blocked_solve_k1<T, W>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 64);
+    if (e == cudaSuccess) done |= bit;
+    return e;
+}
+
 template <typename T, int W>
 static cudaError_t blocked_w(const SolveParams& p, int tile_rows, int grid, int block,
                              cudaStream_t s) {
-    const size_t smem = sizeof(T) * (size_t)tile_rows;  // <= 48 KB, checked by the caller
+    const size_t smem = sizeof(T) * (size_t)tile_rows;  // checked by the caller
+    if (smem > 48 * 1024 - 256) {
+        cudaError_t e = blocked_smem_attr<T, W>();
+        if (e != cudaSuccess) return e;
+    }
     blocked_solve_k1<T, W><<<grid, block, smem, s>>>(p, tile_rows);
     return cudaGetLastError();
 }
@@ -245,7 +267,9 @@ template <typename T>
 static int occ_blocked(int lanes, int block, size_t smem) {
     int nb = 0;
     cudaError_t e = cudaErrorInvalidValue;
-#define SPTRSV_OCC(WW) \
+#define SPTRSV_OCC(WW)                                                                      \
+    e = smem > 48 * 1024 - 256 ? blocked_smem_attr<T, WW>() : cudaSuccess;                   \
+    if (e == cudaSuccess)                                                                    \
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, blocked_solve_k1<T, WW>, block, smem)
     switch (lanes) {
         case 1: SPTRSV_OCC(1); break;

@@ -16,7 +16,8 @@ from ._lib import SptrsvError, check
 
 ALGOS = {"level": _lib.ALGO_LEVEL, "self": _lib.ALGO_SELF, "tiled": _lib.ALGO_SELF_TILED,
          "chains": _lib.ALGO_SELF_CHAINS, "permuted": _lib.ALGO_SELF_PERMUTED,
-         "column": _lib.ALGO_SELF_COLUMN, "blocked": _lib.ALGO_SELF_BLOCKED}
+         "column": _lib.ALGO_SELF_COLUMN, "blocked": _lib.ALGO_SELF_BLOCKED,
+         "partitioned": _lib.ALGO_SELF_PARTITIONED}
 
 
 def _ptr(t):
@@ -252,6 +253,19 @@ class TriangularPlan:
     @property
     def tiling(self):
         return getattr(self, "_tiling", (2048, False))
+
+    def set_partition(self, part_rows=0):
+        """Rows per part of the partitioned solve (algo="partitioned"; 0:
+        the rows divided evenly over the SMs; reduced to what fits shared
+        memory)."""
+        check(_lib.load().sptrsv_set_partition(self._h, int(part_rows)), "sptrsv_set_partition")
+
+    @property
+    def partition(self):
+        """Rows per part the next partitioned solve uses."""
+        v = ctypes.c_int()
+        check(_lib.load().sptrsv_get_partition(self._h, ctypes.byref(v)), "sptrsv_get_partition")
+        return v.value
 
     def set_spin_limit(self, polls):
         check(_lib.load().sptrsv_set_spin_limit(self._h, int(polls)), "sptrsv_set_spin_limit")

@@ -43,7 +43,8 @@ MATRICES = {
 
 _cache = {}
 
-ALL_ALGOS = ("self", "level", "permuted", "blocked", "column", "tiled", "chains")
+ALL_ALGOS = ("self", "level", "permuted", "blocked", "column", "tiled", "chains",
+             "partitioned")
 
 
 def mat(name):
@@ -145,7 +146,7 @@ def test_reanalyze_methods_give_the_same_levels(name, method):
 # ---------------------------------------------------------------- solves
 
 @pytest.mark.parametrize("algo", ["self", "level", "tiled", "tiled_levels", "chains", "permuted",
-                                  "column", "blocked"])
+                                  "column", "blocked", "partitioned"])
 @pytest.mark.parametrize("name", list(MATRICES))
 def test_solve_fp64(name, algo):
     A = mat(name)
@@ -161,7 +162,7 @@ def test_solve_fp64(name, algo):
 
 
 @pytest.mark.parametrize("algo", ["self", "level", "tiled", "chains", "permuted", "column",
-                                  "blocked"])
+                                  "blocked", "partitioned"])
 @pytest.mark.parametrize("name", ["general", "ilu_L", "ilu_U", "long_rows"])
 def test_solve_fp32(name, algo):
     A = mat(name)
@@ -181,9 +182,10 @@ def test_every_launch_shape(lanes, block):
     with plan_for(A) as p:
         p.set_tuning(lanes, block, 0)
         bt = torch.tensor(b, device=dev())
-        for algo in ("self", "level", "chains", "permuted", "column"):
+        for algo in ("self", "level", "chains", "permuted", "column", "partitioned"):
             assert relerr(p.solve(bt, algo=algo), ref) <= TOL64
         p.set_tuning(lanes, block, 3)          # a tiny persistent grid still finishes
+        assert relerr(p.solve(bt, algo="partitioned"), ref) <= TOL64
         assert relerr(p.solve(bt), ref) <= TOL64
         assert relerr(p.solve(bt, algo="chains"), ref) <= TOL64
         assert relerr(p.solve(bt, algo="permuted"), ref) <= TOL64
@@ -240,7 +242,7 @@ def test_multi_rhs_width_does_not_change_results():
 
 
 @pytest.mark.parametrize("algo", ["self", "level", "tiled", "chains", "permuted", "column",
-                                  "blocked"])
+                                  "blocked", "partitioned"])
 def test_leading_dimension_and_in_place(algo):
     A = mat("general")
     k, ld = 3, 5
@@ -262,7 +264,7 @@ def test_leading_dimension_and_in_place(algo):
 
 
 @pytest.mark.parametrize("algo", ["self", "level", "tiled", "tiled_levels", "chains", "permuted",
-                                  "column", "blocked"])
+                                  "column", "blocked", "partitioned"])
 @pytest.mark.parametrize("name", ["workload0", "ilu_L", "ilu_U", "general", "general_upper",
                                   "long_rows", "unit_nodiag", "bidiag"])
 def test_solve_transpose(name, algo):
@@ -309,8 +311,13 @@ def test_bitwise_determinism_and_algo_agreement():
         for tile in (64, 1000, 4096):
             p.set_tiling(tile, False)
             assert torch.equal(p.solve(bt, algo="blocked"), first)
+        # and the partitioned solve, whatever the part size
+        for rows in (0, 1, 77, 1000, 20011, 1 << 20):
+            p.set_partition(rows)
+            assert torch.equal(p.solve(bt, algo="partitioned"), first), rows
         tg = torch.tensor(synth.uniform(A.n, 23), device=dev())
         assert torch.equal(p.solve_transpose(tg, algo="permuted"), p.solve_transpose(tg))
+        assert torch.equal(p.solve_transpose(tg, algo="partitioned"), p.solve_transpose(tg))
         # the column-wise form (Alg. 4) adds contributions atomically in
         # arrival order: equal to rounding only
         for _ in range(3):
@@ -368,7 +375,7 @@ def test_autograd_sees_in_place_value_updates_with_copying_algorithms():
     with plan_for(A) as p:
         v = p.vals
         bt = torch.tensor(b, device=dev())
-        for algo in ("permuted", "blocked"):
+        for algo in ("permuted", "blocked", "partitioned"):
             sparse_triangular_solve(p, v, bt, algo=algo)
             with torch.no_grad():
                 v.mul_(0.5)
@@ -377,26 +384,54 @@ def test_autograd_sees_in_place_value_updates_with_copying_algorithms():
             assert relerr(x.detach(), ref) <= TOL64, algo
 
 
-def test_level_ordered_copy_follows_value_updates():
-    """The level-ordered copy is a snapshot of the values: sptrsv_refresh_values
-    (in-place change) and sptrsv_set_values (new array) bring it up to date,
-    for the forward and the transposed copy."""
+@pytest.mark.parametrize("algo", ["permuted", "partitioned"])
+def test_level_ordered_copy_follows_value_updates(algo):
+    """The level- and part-ordered copies are snapshots of the values:
+    sptrsv_refresh_values (in-place change) and sptrsv_set_values (new array)
+    bring them up to date, for the forward and the transposed copy."""
     A = mat("ilu_U")
     with plan_for(A) as p:
         b = synth.uniform(A.n, 24)
         bt = torch.tensor(b, device=dev())
-        p.solve(bt, algo="permuted")
-        p.solve_transpose(bt, algo="permuted")
+        p.solve(bt, algo=algo)
+        p.solve_transpose(bt, algo=algo)
         p.vals.mul_(2.0)
         p.refresh_values()
         ref = oracle.solve(A.rowptr, A.colidx, 2.0 * A.vals, b, upper=True)
-        assert relerr(p.solve(bt, algo="permuted"), ref) <= TOL64
+        assert relerr(p.solve(bt, algo=algo), ref) <= TOL64
         v3 = torch.tensor(3.0 * A.vals, device=dev())
         p.set_values(v3)
         ref = oracle.solve(A.rowptr, A.colidx, 3.0 * A.vals, b, upper=True)
-        assert relerr(p.solve(bt, algo="permuted"), ref) <= TOL64
+        assert relerr(p.solve(bt, algo=algo), ref) <= TOL64
         reft = oracle.solve_transpose(A.rowptr, A.colidx, 3.0 * A.vals, b, upper=True)
-        assert relerr(p.solve_transpose(bt, algo="permuted"), reft) <= TOL64
+        assert relerr(p.solve_transpose(bt, algo=algo), reft) <= TOL64
+
+
+@pytest.mark.parametrize("name", ["ilu_L", "ilu_U", "general", "general_upper", "bidiag",
+                                  "bidiag_upper", "diag", "long_rows", "unit_nodiag",
+                                  "lap3d_27pt", "lap2d_9pt_upper"])
+def test_partitioned_part_sizes(name):
+    """Parts of one row, ragged last parts, one part for the whole matrix and
+    the automatic size; every lanes-per-row; a grid smaller than the parts.
+    Each lane folds its entries in the order of the self-scheduled kernel,
+    so the results are bitwise equal to it, and within 1e-12 of the oracle."""
+    A = mat(name)
+    b = synth.uniform(A.n, 27)
+    ref = oracle.solve(A.rowptr, A.colidx, A.vals, b, upper=A.upper, unit=A.unit)
+    with plan_for(A) as p:
+        bt = torch.tensor(b, device=dev())
+        for lanes, block, grid in ((1, 128, 0), (4, 256, 0), (32, 1024, 5)):
+            p.set_tuning(lanes, block, grid)
+            p.set_partition(0)
+            first = p.solve(bt)
+            assert relerr(first, ref) <= TOL64
+            for rows in (1, 33, 960, A.n, 0):
+                p.set_partition(rows)
+                assert torch.equal(p.solve(bt, algo="partitioned"), first), (lanes, rows)
+        assert p.status() == (0, -1)
+        p.set_partition(1 << 30)              # reduced to what fits shared memory
+        assert 1000 <= p.partition < (1 << 30)
+        assert relerr(p.solve(bt, algo="partitioned"), ref) <= TOL64
 
 
 def _bad(n, rows, cols, vals, upper=False, unit=False):
@@ -437,7 +472,8 @@ def test_bad_rowptr():
     assert ei.value.status == 2
 
 
-@pytest.mark.parametrize("algo", ["self", "tiled", "chains", "permuted", "column", "blocked"])
+@pytest.mark.parametrize("algo", ["self", "tiled", "chains", "permuted", "column", "blocked",
+                                  "partitioned"])
 def test_timeout_is_reported_and_solve_finishes(algo):
     """A row that is never published: every row that depends on it gives up
     after the spin limit, records SPTRSV_ERR_TIMEOUT and publishes NaN; rows
@@ -598,6 +634,6 @@ def test_autotuner_picks_an_algorithm_and_stays_exact():
         bt = torch.tensor(b, device=dev())
         res = autotune.tune_algos(p, bt, use_cache=False, lanes=(2, 8), blocks=(256,),
                                   grids=(0, 2), tiles=(512, 2048))
-        assert res["algo"] in ("self", "permuted", "blocked", "tiled", "chains")
+        assert res["algo"] in ("self", "permuted", "blocked", "partitioned", "tiled", "chains")
         assert p.best_algo == res["algo"]
         assert relerr(p.solve(bt, algo="auto"), ref) <= TOL64
