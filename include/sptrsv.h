@@ -318,10 +318,21 @@ SPTRSV_API sptrsv_status_t sptrsv_refresh_values(sptrsv_plan_t plan, void *strea
  * many as fit on the device at once; the default is 2 blocks per SM, which
  * keeps enough rows waiting ahead of the dependency frontier without
  * flooding L2 with polls).  Applies to the forward and the transposed
- * solves.  Multi-RHS solves have their own launch shape
- * (sptrsv_set_mrhs_tuning), by default this block size and grid cap. */
+ * solves.  Sets the shape of every algorithm (clearing the shapes set for
+ * single algorithms by sptrsv_set_algo_tuning).  Multi-RHS solves have their
+ * own launch shape (sptrsv_set_mrhs_tuning), by default this block size and
+ * grid cap. */
 SPTRSV_API sptrsv_status_t sptrsv_set_tuning(sptrsv_plan_t plan, int lanes_per_row,
                                   int block_size, int max_blocks);
+/* Launch shape of one algorithm's single-RHS solves, overriding the plan's
+ * shape for it (same ranges as sptrsv_set_tuning; lanes_per_row 0 clears it,
+ * so the algorithm uses the plan's shape again).  Lets an autotuner keep the
+ * best shape of every form it measured: solves that always run one form
+ * (the FP32 solves inside sptrsv_solve_refined run SPTRSV_ALGO_SELF) keep
+ * that form's shape whichever form won overall. */
+SPTRSV_API sptrsv_status_t sptrsv_set_algo_tuning(sptrsv_plan_t plan, sptrsv_algo_t algo,
+                                                  int lanes_per_row, int block_size,
+                                                  int max_blocks);
 SPTRSV_API sptrsv_status_t sptrsv_get_tuning(sptrsv_plan_t plan, int *lanes_per_row,
                                   int *block_size, int *max_blocks);
 

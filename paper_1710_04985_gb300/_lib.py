@@ -49,6 +49,7 @@ SIGNATURES = [
     ("sptrsv_set_tuning", _c_int, [_vp, _c_int, _c_int, _c_int]),
     ("sptrsv_get_tuning", _c_int, [_vp, _ip, _ip, _ip]),
     ("sptrsv_set_mrhs_tuning", _c_int, [_vp, _c_int, _c_int, _c_int]),
+    ("sptrsv_set_algo_tuning", _c_int, [_vp, _c_int, _c_int, _c_int, _c_int]),
     ("sptrsv_set_spin_limit", _c_int, [_vp, _c_ll]),
     ("sptrsv_set_tiling", _c_int, [_vp, _c_int, _c_int]),
     ("sptrsv_set_partition", _c_int, [_vp, _c_int]),

@@ -164,6 +164,10 @@ def tune_algos(plan, b, x=None, algos=("self", "permuted", "blocked", "partition
     _apply(plan, per[name]["best"], name, nrhs)
     if nrhs == 1:  # multi-RHS solves always run the in-place kernel
         plan.best_algo = name
+        # every measured form keeps its own best shape (the FP32 solves of a
+        # refined solve run the in-place form whichever form won)
+        for a, r in per.items():
+            plan.set_algo_tuning(a, *r["best"][:3])
     return {"algo": name, "best": per[name]["best"], "per_algo": per}
 
 

@@ -165,6 +165,10 @@ struct sptrsv_plan_s {
     size_t rd_elems = 0;
     unsigned long long* stats = nullptr;  // [0] max|r| [1] |A|_inf [2] max|x| [3] max|b|
     int lanes = 4, block = 256, max_blocks = 0;
+    // per-algorithm single-RHS shapes (lanes 0: use the plan's shape)
+    int alg_lanes[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int alg_block[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int alg_max_blocks[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     // multi-RHS launch shape: width (0: chosen from nrhs), block (0: the
     // single-RHS one), grid cap (-1: the single-RHS one)
     int mrhs_lanes = 0, mrhs_block = 0, mrhs_max_blocks = -1;
@@ -793,10 +797,16 @@ sptrsv_status_t run_solve(sptrsv_plan_t P, bool trans, bool f64, const void* val
                           long long ldb, void* x, long long ldx, int nrhs, sptrsv_algo_t algo,
                           cudaStream_t s) {
     const bool mrhs = nrhs > 1;
-    // multi-RHS solves have a launch shape of their own (sptrsv_set_mrhs_tuning)
-    const int lanes = mrhs ? (P->mrhs_lanes ? P->mrhs_lanes : mrhs_lanes(nrhs)) : P->lanes;
-    const int block = mrhs && P->mrhs_block ? P->mrhs_block : P->block;
-    const int max_blocks = mrhs && P->mrhs_max_blocks >= 0 ? P->mrhs_max_blocks : P->max_blocks;
+    // multi-RHS solves have a launch shape of their own (sptrsv_set_mrhs_tuning);
+    // a single-RHS solve takes its algorithm's shape if one was set
+    const int a = (int)algo;
+    const bool own = !mrhs && a >= 0 && a < 8 && P->alg_lanes[a] > 0;
+    const int lanes = mrhs ? (P->mrhs_lanes ? P->mrhs_lanes : mrhs_lanes(nrhs))
+                           : (own ? P->alg_lanes[a] : P->lanes);
+    const int block = mrhs ? (P->mrhs_block ? P->mrhs_block : P->block)
+                           : (own ? P->alg_block[a] : P->block);
+    const int max_blocks = mrhs ? (P->mrhs_max_blocks >= 0 ? P->mrhs_max_blocks : P->max_blocks)
+                                : (own ? P->alg_max_blocks[a] : P->max_blocks);
     if (algo == SPTRSV_ALGO_SELF_CHAINS && !mrhs) ST(build_chain(P, trans, lanes, s));
     // the level-ordered copy holds the plan's own element type
     const bool blocked = algo == SPTRSV_ALGO_SELF_BLOCKED && !mrhs && f64 == P->f64;
@@ -1271,6 +1281,26 @@ sptrsv_status_t sptrsv_set_tuning(sptrsv_plan_t plan, int lanes_per_row, int blo
     plan->lanes = w;
     plan->block = block_size;
     plan->max_blocks = max_blocks;
+    for (int a = 0; a < 8; ++a) plan->alg_lanes[a] = 0;
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t sptrsv_set_algo_tuning(sptrsv_plan_t plan, sptrsv_algo_t algo, int lanes_per_row,
+                                       int block_size, int max_blocks) {
+    const int a = (int)algo;
+    if (!plan || a < SPTRSV_ALGO_LEVEL || a > SPTRSV_ALGO_SELF_PARTITIONED)
+        return SPTRSV_ERR_INVALID_ARG;
+    const int w = lanes_per_row;
+    if (w == 0) {
+        plan->alg_lanes[a] = 0;
+        return SPTRSV_OK;
+    }
+    if (!(w == 1 || w == 2 || w == 4 || w == 8 || w == 16 || w == 32)) return SPTRSV_ERR_INVALID_ARG;
+    if (block_size < 32 || block_size > 1024 || block_size % 32 != 0 || max_blocks < 0)
+        return SPTRSV_ERR_INVALID_ARG;
+    plan->alg_lanes[a] = w;
+    plan->alg_block[a] = block_size;
+    plan->alg_max_blocks[a] = max_blocks;
     return SPTRSV_OK;
 }
 

@@ -225,6 +225,13 @@ class TriangularPlan:
         check(_lib.load().sptrsv_set_tuning(self._h, lanes_per_row, block_size, max_blocks),
               "sptrsv_set_tuning")
 
+    def set_algo_tuning(self, algo, lanes_per_row=0, block_size=256, max_blocks=0):
+        """Launch shape of one algorithm's single-RHS solves (lanes_per_row 0:
+        use the plan's shape); ``set_tuning`` clears them all."""
+        check(_lib.load().sptrsv_set_algo_tuning(self._h, ALGOS[algo], int(lanes_per_row),
+                                                 int(block_size), int(max_blocks)),
+              "sptrsv_set_algo_tuning")
+
     def set_mrhs_tuning(self, lanes_per_row=0, block_size=0, max_blocks=-1):
         """Launch shape of multi-RHS solves: width (0: one lane per column up
         to 16), block size (0) and grid cap (-1) default to the single-RHS

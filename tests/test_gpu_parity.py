@@ -197,6 +197,36 @@ def test_every_launch_shape(lanes, block):
                 assert relerr(p.solve(bt, algo="blocked"), ref) <= TOL64
 
 
+def test_per_algorithm_launch_shape():
+    """sptrsv_set_algo_tuning gives one algorithm its own launch shape over the
+    plan's; sptrsv_set_tuning clears every such override.  Widths 1 and 32
+    fold a row in different trees, so the results show which shape ran."""
+    from paper_1710_04985_gb300 import SptrsvError
+    A = mat("general")
+    b = synth.uniform(A.n, 28)
+    ref = oracle.solve(A.rowptr, A.colidx, A.vals, b)
+    with plan_for(A) as p:
+        bt = torch.tensor(b, device=dev())
+        p.set_tuning(32, 1024, 3)
+        w32 = p.solve(bt).clone()
+        p.set_tuning(1, 128, 0)
+        w1 = p.solve(bt).clone()
+        assert relerr(w32, ref) <= TOL64 and relerr(w1, ref) <= TOL64
+        assert not torch.equal(w1, w32)
+        p.set_algo_tuning("self", 32, 1024, 3)
+        assert torch.equal(p.solve(bt), w32)                   # its own shape
+        assert torch.equal(p.solve(bt, algo="permuted"), w1)   # the plan's shape
+        p.set_algo_tuning("permuted", 32, 256, 0)
+        assert torch.equal(p.solve(bt, algo="permuted"), w32)
+        p.set_algo_tuning("self", 0)                           # cleared: the plan's shape
+        assert torch.equal(p.solve(bt), w1)
+        p.set_tuning(1, 128, 0)                                # clears every override
+        assert torch.equal(p.solve(bt, algo="permuted"), w1)
+        for bad in ((3, 256, 0), (4, 48, 0), (4, 256, -1)):
+            with pytest.raises(SptrsvError):
+                p.set_algo_tuning("self", *bad)
+
+
 @pytest.mark.parametrize("k", [2, 3, 8, 32, 33])
 @pytest.mark.parametrize("algo", ["self", "level", "tiled", "chains"])
 def test_multi_rhs(k, algo):
