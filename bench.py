@@ -511,7 +511,8 @@ def main():
                        "tuning": {"L": _tuning_row(tune_l), "U": _tuning_row(tune_u),
                                   "fields": ["lanes_per_row", "block", "max_blocks",
                                              "tile_rows (part_rows when partitioned; 0: "
-                                             "automatic)", "tile_level_order"]},
+                                             "automatic)", "tile_level_order (cluster "
+                                             "blocks when partitioned)"]},
                        "l2": "inputs larger than L2 (2 x 150 MB of matrix+vectors per step)",
                        "parallelism": f"replicas x{world}"},
             "effective_gbs": value * bytes_solve / 1e9,
@@ -710,11 +711,13 @@ def _break_even(setup_a, solve_a, setup_b, solve_b):
 
 
 def _tuning_row(t):
-    """lanes, block, max_blocks, tile (or part) rows, tile level order."""
+    """lanes, block, max_blocks, tile (or part) rows, tile level order (or,
+    partitioned, the cluster size)."""
     best = t["best"]
     sized = t["algo"] in ("tiled", "blocked", "partitioned")
-    return [best[0], best[1], best[2], best[4] if sized else None,
-            bool(best[5]) if t["algo"] == "tiled" else None]
+    last = (bool(best[5]) if t["algo"] == "tiled"
+            else (int(best[5]) or 1) if t["algo"] == "partitioned" else None)
+    return [best[0], best[1], best[2], best[4] if sized else None, last]
 
 
 def _events_ms(fn, reps):

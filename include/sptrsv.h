@@ -355,17 +355,24 @@ SPTRSV_API sptrsv_status_t sptrsv_set_mrhs_tuning(sptrsv_plan_t plan, int lanes_
 SPTRSV_API sptrsv_status_t sptrsv_set_tiling(sptrsv_plan_t plan, int tile_rows,
                                              int level_order);
 
-/* Rows per part of SPTRSV_ALGO_SELF_PARTITIONED (0: automatic, the rows
- * divided evenly over the GPU's SMs).  A part's unknowns must fit one thread
- * block's shared memory: larger values are reduced to the largest part that
- * fits (29,024 rows in FP64 and 58,048 in FP32 with 227 KB per block).  The
- * part-ordered copy is rebuilt on the next partitioned solve.  part_rows < 0
- * is SPTRSV_ERR_INVALID_ARG. */
-SPTRSV_API sptrsv_status_t sptrsv_set_partition(sptrsv_plan_t plan, int part_rows);
+/* Parts of SPTRSV_ALGO_SELF_PARTITIONED.  part_rows: rows per part (0:
+ * automatic, the rows divided evenly over the GPU's SMs).  A part's unknowns
+ * must fit one thread block's shared memory: larger values are reduced to the
+ * largest part that fits (29,024 rows in FP64 and 58,048 in FP32 with 227 KB
+ * per block).  cluster_blocks in {0, 1, 2, 4, 8}: with 2 or more, thread-block
+ * clusters of that many blocks take consecutive parts together and read the
+ * values of the cluster's earlier parts from those blocks' shared memory
+ * (distributed shared memory) instead of waiting on L2; 0 and 1 use no
+ * clusters (the default).  The part-ordered copy is rebuilt on the next
+ * partitioned solve when part_rows changes.  Other values are
+ * SPTRSV_ERR_INVALID_ARG. */
+SPTRSV_API sptrsv_status_t sptrsv_set_partition(sptrsv_plan_t plan, int part_rows,
+                                                int cluster_blocks);
 
 /* The part size the next partitioned solve uses (after the automatic choice
- * and the shared-memory limit). */
-SPTRSV_API sptrsv_status_t sptrsv_get_partition(sptrsv_plan_t plan, int *part_rows);
+ * and the shared-memory limit) and its cluster size (1: no clusters). */
+SPTRSV_API sptrsv_status_t sptrsv_get_partition(sptrsv_plan_t plan, int *part_rows,
+                                                int *cluster_blocks);
 
 /* Upper bound on the polling rounds of one dependency wait before the wait
  * gives up, records SPTRSV_ERR_TIMEOUT with its row and goes on with NaN so

@@ -25,6 +25,7 @@ BLOCKS = (128, 256, 512)
 GRID_FRACTIONS = (0, 4, 2, 1)      # max_blocks = fraction * SMs (0: as many as fit)
 TILES = (1024, 2048, 4096)
 PARTS = (0, 4096, 8192, 16384)     # rows per part of the partitioned form (0: automatic)
+CLUSTERS = (2, 4)                  # thread-block cluster sizes tried for the partitioned form
 TILED = ("tiled", "blocked", "partitioned")   # forms with a tile (or part) size
 TILE_ORDERS = (False, True)      # substitution order, level order
 
@@ -51,12 +52,15 @@ def time_solve(plan, b, x, algo="self", reps=3, transpose=False):
 
 
 def tune(plan, b, x=None, algo="self", lanes=LANES, blocks=BLOCKS, grids=GRID_FRACTIONS,
-         tiles=TILES, reps=3, use_cache=True, transpose=False, tile_orders=TILE_ORDERS):
+         tiles=TILES, reps=3, use_cache=True, transpose=False, tile_orders=TILE_ORDERS,
+         clusters=CLUSTERS):
     """Pick lanes-per-row, block size, grid cap (and tile size for "tiled")
     for `plan` on `b`.
 
     Sets the winner on the plan and returns ``{"best": (lanes, block,
-    max_blocks, ms, tile_rows, level_order), "table": [...]}``."""
+    max_blocks, ms, tile_rows, level_order), "table": [...]}`` (for the
+    partitioned form tile_rows is the part size and the last field the
+    thread-block cluster size)."""
     nrhs = 1 if b.dim() == 1 else b.shape[1]
     mrhs = nrhs > 1 and algo in ("self", "level")
     if mrhs:
@@ -83,8 +87,8 @@ def tune(plan, b, x=None, algo="self", lanes=LANES, blocks=BLOCKS, grids=GRID_FR
             plan.set_mrhs_tuning(w, blk, mb)
         else:
             plan.set_tuning(w, blk, mb)
-        if algo == "partitioned":
-            plan.set_partition(tile)
+        if algo == "partitioned":  # `order` holds the cluster size here
+            plan.set_partition(tile, int(order) if order else 1)
         elif tiles_used:
             plan.set_tiling(tile, order)
         ms = time_solve(plan, b, x, algo, reps, transpose)
@@ -112,6 +116,10 @@ def tune(plan, b, x=None, algo="self", lanes=LANES, blocks=BLOCKS, grids=GRID_FR
             # parts are reduced to what fits shared memory by the library
             if tile != tile0 and (algo == "partitioned" or tile * esize <= 48 * 1024 - 256):
                 run(bb[0], bb[1], bb[2], tile, bb[5])
+    if algo == "partitioned":
+        bb = min(table, key=lambda r: r[3])
+        for cl in clusters:
+            run(bb[0], bb[1], bb[2], bb[4], cl)
     best = min(table, key=lambda r: r[3])
     _apply(plan, best, algo, nrhs)
     result = {"best": best, "table": table, "nrhs": nrhs}
@@ -127,7 +135,7 @@ def _apply(plan, best, algo, nrhs=1):
     else:
         plan.set_tuning(best[0], best[1], best[2])
     if algo == "partitioned":
-        plan.set_partition(best[4])
+        plan.set_partition(best[4], int(best[5]) if best[5] else 1)
     elif algo in ("tiled", "blocked"):
         plan.set_tiling(best[4], best[5])
 
@@ -173,10 +181,11 @@ def tune_algos(plan, b, x=None, algos=("self", "permuted", "blocked", "partition
 
 def choice(result):
     """The winning (algo, lanes, block, max_blocks, tile_rows, level_order) of
-    a ``tune_algos`` result, JSON-serialisable."""
+    a ``tune_algos`` result, JSON-serialisable (for the partitioned form:
+    part rows and cluster size in the last two)."""
     best = result["best"]
-    return [result["algo"], int(best[0]), int(best[1]), int(best[2]), int(best[4]),
-            bool(best[5])]
+    last = int(best[5]) if result["algo"] == "partitioned" else bool(best[5])
+    return [result["algo"], int(best[0]), int(best[1]), int(best[2]), int(best[4]), last]
 
 
 def apply_choice(plan, ch):

@@ -175,6 +175,7 @@ struct sptrsv_plan_s {
     int tile_rows = 2048;
     bool tile_level_order = false;
     int part_rows = 0;   // partitioned solve: rows per part (0: automatic)
+    int part_cluster = 1;  // partitioned solve: blocks per thread-block cluster
     int smem_optin = 0;  // shared memory a block may opt in to
     SpinPolicy spin{1ll << 24, 256, 128};
     int withhold = -1;
@@ -885,13 +886,17 @@ sptrsv_status_t run_solve(sptrsv_plan_t P, bool trans, bool f64, const void* val
         p.jlev = L.qord;
         CK(launch_prep_self(f64, P->n, 1, L.xq, 1, nullptr, 0, nullptr, P->counters,
                             P->num_sms * 8, s));
+        const int cl = P->part_cluster;
         const long long tiles = ((long long)P->n + L.qS - 1) / L.qS;
-        long long grid = (long long)blocked_blocks_per_sm(f64, lanes, block, L.qS) * P->num_sms;
+        const long long groups = (tiles + cl - 1) / cl;
+        long long grid = blocked_resident_blocks(f64, lanes, cl, block, L.qS, P->num_sms);
+        if (grid < cl) return SPTRSV_ERR_INVALID_ARG;  // this shape cannot run
         if (max_blocks > 0 && grid > max_blocks) grid = max_blocks;
-        if (grid > tiles) grid = tiles;
-        if (grid < 1) grid = 1;
+        if (grid > groups * cl) grid = groups * cl;
+        grid = grid / cl * cl;
+        if (grid < cl) grid = cl;
         ST(prof_begin(P, s));
-        CK(launch_blocked_k1(f64, lanes, p, L.qS, (int)grid, block, s));
+        CK(launch_blocked_k1(f64, lanes, p, L.qS, (int)grid, block, s, cl));
         ST(prof_end(P, s));
         launches = 2;
     } else if (permuted) {
@@ -910,8 +915,8 @@ sptrsv_status_t run_solve(sptrsv_plan_t P, bool trans, bool f64, const void* val
         const long long want_blocks = (tickets + block / 32 - 1) / (block / 32);
         if (blocked) {
             const long long tiles = ((long long)P->n + P->tile_rows - 1) / P->tile_rows;
-            long long grid = (long long)blocked_blocks_per_sm(f64, lanes, block, P->tile_rows) *
-                             P->num_sms;
+            long long grid = blocked_resident_blocks(f64, lanes, 1, block, P->tile_rows,
+                                                     P->num_sms);
             if (max_blocks > 0 && grid > max_blocks) grid = max_blocks;
             if (grid > tiles) grid = tiles;
             if (grid < 1) grid = 1;
@@ -1337,15 +1342,19 @@ sptrsv_status_t sptrsv_set_tiling(sptrsv_plan_t plan, int tile_rows, int level_o
     return SPTRSV_OK;
 }
 
-sptrsv_status_t sptrsv_set_partition(sptrsv_plan_t plan, int part_rows) {
-    if (!plan || part_rows < 0) return SPTRSV_ERR_INVALID_ARG;
+sptrsv_status_t sptrsv_set_partition(sptrsv_plan_t plan, int part_rows, int cluster_blocks) {
+    const int c = cluster_blocks;
+    if (!plan || part_rows < 0 || !(c == 0 || c == 1 || c == 2 || c == 4 || c == 8))
+        return SPTRSV_ERR_INVALID_ARG;
     plan->part_rows = part_rows;
+    plan->part_cluster = c > 1 ? c : 1;
     return SPTRSV_OK;
 }
 
-sptrsv_status_t sptrsv_get_partition(sptrsv_plan_t plan, int* part_rows) {
-    if (!plan || !part_rows) return SPTRSV_ERR_INVALID_ARG;
+sptrsv_status_t sptrsv_get_partition(sptrsv_plan_t plan, int* part_rows, int* cluster_blocks) {
+    if (!plan || !part_rows || !cluster_blocks) return SPTRSV_ERR_INVALID_ARG;
     *part_rows = resolve_part_rows(plan);
+    *cluster_blocks = plan->part_cluster;
     return SPTRSV_OK;
 }
 

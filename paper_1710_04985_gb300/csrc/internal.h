@@ -84,9 +84,14 @@ int column_blocks_per_sm(bool f64, int lanes, bool cmap, int block);
 // (solve_blocked.cu): a block per tile of tile_rows consecutive positions,
 // in-tile dependencies through shared memory (tile_rows * element size at
 // most the device's opt-in shared memory per block, minus 64 B).
+// cluster in {1, 2, 4, 8}: clusters of that many blocks take consecutive
+// tiles together and read each other's tiles in distributed shared memory;
+// grid must then be a multiple of cluster.
 cudaError_t launch_blocked_k1(bool f64, int lanes, const SolveParams& p, int tile_rows, int grid,
-                              int block, cudaStream_t s);
-int blocked_blocks_per_sm(bool f64, int lanes, int block, int tile_rows);
+                              int block, cudaStream_t s, int cluster = 1);
+// Blocks of one launch that can be resident at once (0: the shape cannot run).
+int blocked_resident_blocks(bool f64, int lanes, int cluster, int block, int tile_rows,
+                            int num_sms);
 // Resident blocks per SM of the level-ordered-copy form of self_solve_k1.
 int self_perm_blocks_per_sm(bool f64, int lanes, int block);
 

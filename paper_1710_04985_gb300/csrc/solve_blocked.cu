@@ -43,12 +43,69 @@ __device__ __forceinline__ void sts_volatile(T* p, T v) {
     *(volatile T*)p = v;
 }
 
-template <typename T, int W>
+// ---- thread-block clusters: distributed shared memory of the cluster's blocks
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// Every thread of every block of the cluster; orders shared-memory accesses
+// around it across the cluster.
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;"
+                 ::: "memory");
+}
+// Address of `local` (this block's shared memory) in block `rank`'s.
+__device__ __forceinline__ unsigned cluster_addr(const void* local, unsigned rank) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(local);
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ double ld_cluster(unsigned a, double) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.cluster.shared::cluster.b64 %0, [%1];" : "=l"(v) : "r"(a) : "memory");
+    return __longlong_as_double((long long)v);
+}
+__device__ __forceinline__ float ld_cluster(unsigned a, float) {
+    unsigned v;
+    asm volatile("ld.relaxed.cluster.shared::cluster.b32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return __uint_as_float(v);
+}
+__device__ __forceinline__ int ld_cluster_int(unsigned a) {
+    int v;
+    asm volatile("ld.relaxed.cluster.shared::cluster.b32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+// Publication into this block's shared memory, visible to the cluster.
+__device__ __forceinline__ void st_cluster(double* p, double v) {
+    asm volatile("st.relaxed.cluster.shared::cta.b64 [%0], %1;" ::"r"(
+                     (unsigned)__cvta_generic_to_shared(p)),
+                 "l"((unsigned long long)__double_as_longlong(v))
+                 : "memory");
+}
+__device__ __forceinline__ void st_cluster(float* p, float v) {
+    asm volatile("st.relaxed.cluster.shared::cta.b32 [%0], %1;" ::"r"(
+                     (unsigned)__cvta_generic_to_shared(p)),
+                 "r"(__float_as_uint(v))
+                 : "memory");
+}
+
+// CS > 1: a cluster of CS blocks takes CS consecutive tiles at once (one
+// ticket), block r the r-th; a dependency on one of the earlier tiles of the
+// same group is read from that block's shared memory (distributed shared
+// memory, no L2 round trip), one on an earlier group from the publication
+// buffer.  Three cluster barriers per group: after the ticket is taken,
+// after every block has read it and reset its tile (no block reads a stale
+// tile of another), and when every block is done (no block reuses, or exits
+// with, shared memory another still reads).
+template <typename T, int W, int CS>
 __global__ void __launch_bounds__(1024) blocked_solve_k1(SolveParams p, int tile_rows) {
     extern __shared__ __align__(16) unsigned char blocked_smem[];
     T* xs = (T*)blocked_smem;
     __shared__ int s_tile;
     __shared__ int s_next;
+    const unsigned crank = CS > 1 ? cluster_rank() : 0u;
     constexpr int R = 32 / W;
     constexpr int E = kChunk;
     constexpr unsigned FULL = 0xffffffffu;
@@ -62,16 +119,36 @@ __global__ void __launch_bounds__(1024) blocked_solve_k1(SolveParams p, int tile
     T* xp = (T*)p.xp;  // publication buffer, position order
     const int n = p.n;
     while (true) {
-        if (threadIdx.x == 0) {
-            s_tile = atomicAdd(p.ticket, 1);
-            s_next = 0;
+        long long p0, g0 = 0;  // this block's tile, and its group's first position
+        if (CS == 1) {
+            if (threadIdx.x == 0) {
+                s_tile = atomicAdd(p.ticket, 1);
+                s_next = 0;
+            }
+            __syncthreads();
+            p0 = (long long)s_tile * tile_rows;
+            if (p0 >= n) break;
+        } else {
+            if (crank == 0 && threadIdx.x == 0) s_tile = atomicAdd(p.ticket, 1);
+            cluster_sync();
+            const int t = crank == 0 ? s_tile : ld_cluster_int(cluster_addr(&s_tile, 0));
+            g0 = (long long)t * CS * tile_rows;
+            p0 = g0 + (long long)crank * tile_rows;
+            if (threadIdx.x == 0) s_next = 0;
+            if (p0 < n) {
+                const int m = (int)((n - p0) < tile_rows ? (n - p0) : tile_rows);
+                for (int k = threadIdx.x; k < m; k += blockDim.x)
+                    xs[k] = Marker<T>::pending_value();
+            }
+            cluster_sync();
+            if (g0 >= n) break;  // the same for the whole cluster
         }
-        __syncthreads();
-        const long long p0 = (long long)s_tile * tile_rows;
-        if (p0 >= n) break;
-        const int in_tile = (int)((n - p0) < tile_rows ? (n - p0) : tile_rows);
-        for (int k = threadIdx.x; k < in_tile; k += blockDim.x) xs[k] = Marker<T>::pending_value();
-        {  // the tile's rows are contiguous in the copy: one L2 prefetch per 128 B line
+        const int in_tile =
+            p0 >= n ? 0 : (int)((n - p0) < tile_rows ? (n - p0) : tile_rows);
+        if (CS == 1)
+            for (int k = threadIdx.x; k < in_tile; k += blockDim.x)
+                xs[k] = Marker<T>::pending_value();
+        if (in_tile > 0) {  // the tile's rows are contiguous in the copy: one L2 prefetch per 128 B line
             const long long q0 = p.ptr[p0], q1 = p.ptr[p0 + in_tile];
             for (long long q = q0 + 32ll * threadIdx.x; q < q1; q += 32ll * blockDim.x)
                 prefetch_l2(p.idx + q);
@@ -106,11 +183,18 @@ __global__ void __launch_bounds__(1024) blocked_solve_k1(SolveParams p, int tile
             }
             if (W > 1 && !p.unit) dinv = __shfl_sync(FULL, dinv, grp * W);
             int q0 = beg + sl;
-            int c[E];  // position of the dependency, or its offset in the tile
+            // position of the dependency, its offset in the tile, or (remote)
+            // its address in another block's shared memory
+            int c[E];
             T a[E], v[E];
-            unsigned live = 0, pend = 0, local = 0;
+            unsigned live = 0, pend = 0, local = 0, remote = 0;
+            auto poll = [&](int e) -> T {
+                if (local & (1u << e)) return lds_volatile(xs + c[e]);
+                if (CS > 1 && (remote & (1u << e))) return ld_cluster((unsigned)c[e], T(0));
+                return ld_relaxed(xp + c[e]);
+            };
             auto load_chunk = [&]() {
-                live = pend = local = 0;
+                live = pend = local = remote = 0;
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     const int q = q0 + e * W;
@@ -125,6 +209,11 @@ __global__ void __launch_bounds__(1024) blocked_solve_k1(SolveParams p, int tile
                             if (cc >= p0) {
                                 c[e] = (int)(cc - p0);
                                 local |= 1u << e;
+                            } else if (CS > 1 && cc >= g0) {
+                                const long long o = cc - g0;
+                                c[e] = (int)cluster_addr(xs + (int)(o % tile_rows),
+                                                         (unsigned)(o / tile_rows));
+                                remote |= 1u << e;
                             } else {
                                 c[e] = cc;
                             }
@@ -134,7 +223,7 @@ __global__ void __launch_bounds__(1024) blocked_solve_k1(SolveParams p, int tile
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     if (!(live & (1u << e))) continue;
-                    v[e] = (local & (1u << e)) ? lds_volatile(xs + c[e]) : ld_relaxed(xp + c[e]);
+                    v[e] = poll(e);
                 }
                 if (!p.unit) {
 #pragma unroll
@@ -163,7 +252,10 @@ __global__ void __launch_bounds__(1024) blocked_solve_k1(SolveParams p, int tile
                     const T tot = group_sum<W>(sum, FULL);
                     if (fresh && sl == 0 && i != p.withhold) {
                         const T xi = publishable(tot);
-                        sts_volatile(xs + off, xi);
+                        if (CS > 1)
+                            st_cluster(xs + off, xi);
+                        else
+                            sts_volatile(xs + off, xi);
                         st_relaxed(xp + k, xi);
                         x[(long long)i * p.ldx] = xi;
                     }
@@ -179,8 +271,7 @@ __global__ void __launch_bounds__(1024) blocked_solve_k1(SolveParams p, int tile
 #pragma unroll
                         for (int e = 0; e < E; ++e) {
                             if (!(pend & (1u << e))) continue;
-                            v[e] = (local & (1u << e)) ? lds_volatile(xs + c[e])
-                                                       : ld_relaxed(xp + c[e]);
+                            v[e] = poll(e);
                         }
 #pragma unroll
                         for (int e = 0; e < E; ++e)
@@ -198,7 +289,8 @@ __global__ void __launch_bounds__(1024) blocked_solve_k1(SolveParams p, int tile
                             break;
                         }
                         if (__any_sync(FULL, pend != before)) break;
-                        if (waits >= p.spin.hot && __any_sync(FULL, (pend & ~local) != 0)) {
+                        if (waits >= p.spin.hot &&
+                            __any_sync(FULL, (pend & ~local & ~remote) != 0)) {
                             __nanosleep(ns);  // back off only while an L2 dependency is pending
                             ns = ns < p.spin.max_ns ? ns * 2 : p.spin.max_ns;
                         }
@@ -209,14 +301,17 @@ __global__ void __launch_bounds__(1024) blocked_solve_k1(SolveParams p, int tile
                 }
             }
         }
-        __syncthreads();  // every group of the tile is done before xs is reused
+        if (CS == 1)
+            __syncthreads();  // every group of the tile is done before xs is reused
+        else
+            cluster_sync();  // ... and no other block of the cluster still reads it
     }
 }
 
-// Lets blocked_solve_k1<T, W> take the device's opt-in shared memory (tiles
-// beyond 48 KB; once per device).
-template <typename T, int W>
-static cudaError_t blocked_smem_attr() {
+// Lets blocked_solve_k1<T, W, CS> take the device's opt-in shared memory
+// (tiles beyond 48 KB; once per device).
+template <typename T, int W, int CS>
+static cudaError_t blocked_attrs() {
     static unsigned long long done = 0;  // one bit per device
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -225,67 +320,127 @@ static cudaError_t blocked_smem_attr() {
     if (done & bit) return cudaSuccess;
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(blocked_solve_k1<T, W>,
+        e = cudaFuncSetAttribute(blocked_solve_k1<T, W, CS>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 64);
     if (e == cudaSuccess) done |= bit;
     return e;
 }
 
-template <typename T, int W>
+template <int CS>
+static cudaLaunchConfig_t blocked_config(int grid, int block, size_t smem, cudaStream_t s,
+                                         cudaLaunchAttribute* attr) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid, 1, 1);
+    cfg.blockDim = dim3((unsigned)block, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+template <typename T, int W, int CS>
 static cudaError_t blocked_w(const SolveParams& p, int tile_rows, int grid, int block,
                              cudaStream_t s) {
     const size_t smem = sizeof(T) * (size_t)tile_rows;  // checked by the caller
-    if (smem > 48 * 1024 - 256) {
-        cudaError_t e = blocked_smem_attr<T, W>();
+    if (smem > 48 * 1024 - 256 || CS > 1) {
+        cudaError_t e = blocked_attrs<T, W, CS>();
         if (e != cudaSuccess) return e;
     }
-    blocked_solve_k1<T, W><<<grid, block, smem, s>>>(p, tile_rows);
-    return cudaGetLastError();
+    if (CS == 1) {
+        blocked_solve_k1<T, W, 1><<<grid, block, smem, s>>>(p, tile_rows);
+        return cudaGetLastError();
+    }
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = blocked_config<CS>(grid, block, smem, s, attr);  // grid % CS == 0
+    return cudaLaunchKernelEx(&cfg, blocked_solve_k1<T, W, CS>, p, tile_rows);
+}
+
+template <typename T, int W>
+static cudaError_t blocked_c(int cluster, const SolveParams& p, int tile_rows, int grid,
+                             int block, cudaStream_t s) {
+    switch (cluster) {
+        case 1: return blocked_w<T, W, 1>(p, tile_rows, grid, block, s);
+        case 2: return blocked_w<T, W, 2>(p, tile_rows, grid, block, s);
+        case 4: return blocked_w<T, W, 4>(p, tile_rows, grid, block, s);
+        case 8: return blocked_w<T, W, 8>(p, tile_rows, grid, block, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 template <typename T>
-static cudaError_t blocked_t(int lanes, const SolveParams& p, int tile_rows, int grid, int block,
-                             cudaStream_t s) {
+static cudaError_t blocked_t(int lanes, int cluster, const SolveParams& p, int tile_rows,
+                             int grid, int block, cudaStream_t s) {
     switch (lanes) {
-        case 1: return blocked_w<T, 1>(p, tile_rows, grid, block, s);
-        case 2: return blocked_w<T, 2>(p, tile_rows, grid, block, s);
-        case 4: return blocked_w<T, 4>(p, tile_rows, grid, block, s);
-        case 8: return blocked_w<T, 8>(p, tile_rows, grid, block, s);
-        case 16: return blocked_w<T, 16>(p, tile_rows, grid, block, s);
-        case 32: return blocked_w<T, 32>(p, tile_rows, grid, block, s);
+        case 1: return blocked_c<T, 1>(cluster, p, tile_rows, grid, block, s);
+        case 2: return blocked_c<T, 2>(cluster, p, tile_rows, grid, block, s);
+        case 4: return blocked_c<T, 4>(cluster, p, tile_rows, grid, block, s);
+        case 8: return blocked_c<T, 8>(cluster, p, tile_rows, grid, block, s);
+        case 16: return blocked_c<T, 16>(cluster, p, tile_rows, grid, block, s);
+        case 32: return blocked_c<T, 32>(cluster, p, tile_rows, grid, block, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_blocked_k1(bool f64, int lanes, const SolveParams& p, int tile_rows, int grid,
-                              int block, cudaStream_t s) {
-    return f64 ? blocked_t<double>(lanes, p, tile_rows, grid, block, s)
-               : blocked_t<float>(lanes, p, tile_rows, grid, block, s);
+                              int block, cudaStream_t s, int cluster) {
+    return f64 ? blocked_t<double>(lanes, cluster, p, tile_rows, grid, block, s)
+               : blocked_t<float>(lanes, cluster, p, tile_rows, grid, block, s);
+}
+
+// Resident blocks of one launch: per SM times SMs without clusters, whole
+// clusters times the cluster size with them.
+template <typename T, int W, int CS>
+static int occ_blocked_w(int block, size_t smem, int num_sms) {
+    if ((smem > 48 * 1024 - 256 || CS > 1) && blocked_attrs<T, W, CS>() != cudaSuccess) return 0;
+    if (CS == 1) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, blocked_solve_k1<T, W, 1>, block,
+                                                          smem) != cudaSuccess)
+            return 0;
+        return nb * num_sms;
+    }
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = blocked_config<CS>(CS, block, smem, nullptr, attr);
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, blocked_solve_k1<T, W, CS>, &cfg) != cudaSuccess)
+        return 0;
+    return nc * CS;
+}
+
+template <typename T, int W>
+static int occ_blocked_c(int cluster, int block, size_t smem, int num_sms) {
+    switch (cluster) {
+        case 1: return occ_blocked_w<T, W, 1>(block, smem, num_sms);
+        case 2: return occ_blocked_w<T, W, 2>(block, smem, num_sms);
+        case 4: return occ_blocked_w<T, W, 4>(block, smem, num_sms);
+        case 8: return occ_blocked_w<T, W, 8>(block, smem, num_sms);
+        default: return 0;
+    }
 }
 
 template <typename T>
-static int occ_blocked(int lanes, int block, size_t smem) {
-    int nb = 0;
-    cudaError_t e = cudaErrorInvalidValue;
-#define SPTRSV_OCC(WW)                                                                      \
-    e = smem > 48 * 1024 - 256 ? blocked_smem_attr<T, WW>() : cudaSuccess;                   \
-    if (e == cudaSuccess)                                                                    \
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, blocked_solve_k1<T, WW>, block, smem)
+static int occ_blocked(int lanes, int cluster, int block, size_t smem, int num_sms) {
     switch (lanes) {
-        case 1: SPTRSV_OCC(1); break;
-        case 2: SPTRSV_OCC(2); break;
-        case 4: SPTRSV_OCC(4); break;
-        case 8: SPTRSV_OCC(8); break;
-        case 16: SPTRSV_OCC(16); break;
-        case 32: SPTRSV_OCC(32); break;
+        case 1: return occ_blocked_c<T, 1>(cluster, block, smem, num_sms);
+        case 2: return occ_blocked_c<T, 2>(cluster, block, smem, num_sms);
+        case 4: return occ_blocked_c<T, 4>(cluster, block, smem, num_sms);
+        case 8: return occ_blocked_c<T, 8>(cluster, block, smem, num_sms);
+        case 16: return occ_blocked_c<T, 16>(cluster, block, smem, num_sms);
+        case 32: return occ_blocked_c<T, 32>(cluster, block, smem, num_sms);
+        default: return 0;
     }
-#undef SPTRSV_OCC
-    return (e == cudaSuccess && nb > 0) ? nb : 1;
 }
 
-int blocked_blocks_per_sm(bool f64, int lanes, int block, int tile_rows) {
+int blocked_resident_blocks(bool f64, int lanes, int cluster, int block, int tile_rows,
+                            int num_sms) {
     const size_t smem = (f64 ? 8 : 4) * (size_t)tile_rows;
-    return f64 ? occ_blocked<double>(lanes, block, smem) : occ_blocked<float>(lanes, block, smem);
+    return f64 ? occ_blocked<double>(lanes, cluster, block, smem, num_sms)
+               : occ_blocked<float>(lanes, cluster, block, smem, num_sms);
 }
 
 }  // namespace sptrsv

@@ -261,18 +261,26 @@ class TriangularPlan:
     def tiling(self):
         return getattr(self, "_tiling", (2048, False))
 
-    def set_partition(self, part_rows=0):
-        """Rows per part of the partitioned solve (algo="partitioned"; 0:
-        the rows divided evenly over the SMs; reduced to what fits shared
-        memory)."""
-        check(_lib.load().sptrsv_set_partition(self._h, int(part_rows)), "sptrsv_set_partition")
+    def set_partition(self, part_rows=0, cluster_blocks=1):
+        """Parts of the partitioned solve (algo="partitioned"): rows per part
+        (0: the rows divided evenly over the SMs; reduced to what fits shared
+        memory) and thread-block cluster size (1, 2, 4, 8: clusters read the
+        values of their earlier parts in distributed shared memory)."""
+        check(_lib.load().sptrsv_set_partition(self._h, int(part_rows), int(cluster_blocks)),
+              "sptrsv_set_partition")
 
     @property
     def partition(self):
         """Rows per part the next partitioned solve uses."""
-        v = ctypes.c_int()
-        check(_lib.load().sptrsv_get_partition(self._h, ctypes.byref(v)), "sptrsv_get_partition")
-        return v.value
+        return self.partition_shape[0]
+
+    @property
+    def partition_shape(self):
+        """(rows per part, cluster blocks) of the next partitioned solve."""
+        v, c = ctypes.c_int(), ctypes.c_int()
+        check(_lib.load().sptrsv_get_partition(self._h, ctypes.byref(v), ctypes.byref(c)),
+              "sptrsv_get_partition")
+        return v.value, c.value
 
     def set_spin_limit(self, polls):
         check(_lib.load().sptrsv_set_spin_limit(self._h, int(polls)), "sptrsv_set_spin_limit")

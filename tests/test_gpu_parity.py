@@ -456,12 +456,17 @@ def test_partitioned_part_sizes(name):
             first = p.solve(bt)
             assert relerr(first, ref) <= TOL64
             for rows in (1, 33, 960, A.n, 0):
-                p.set_partition(rows)
-                assert torch.equal(p.solve(bt, algo="partitioned"), first), (lanes, rows)
+                for cl in (1, 2, 8):             # thread-block clusters of parts
+                    p.set_partition(rows, cl)
+                    assert torch.equal(p.solve(bt, algo="partitioned"), first), (lanes, rows, cl)
         assert p.status() == (0, -1)
-        p.set_partition(1 << 30)              # reduced to what fits shared memory
-        assert 1000 <= p.partition < (1 << 30)
+        p.set_partition(1 << 30, 4)           # reduced to what fits shared memory
+        assert 1000 <= p.partition < (1 << 30) and p.partition_shape[1] == 4
         assert relerr(p.solve(bt, algo="partitioned"), ref) <= TOL64
+        from paper_1710_04985_gb300 import SptrsvError
+        for bad in ((-1, 1), (0, 3), (0, 16)):
+            with pytest.raises(SptrsvError):
+                p.set_partition(*bad)
 
 
 def _bad(n, rows, cols, vals, upper=False, unit=False):

@@ -78,6 +78,9 @@ class _FakePlan:
     def set_tiling(self, tile_rows, level_order=False):
         self.calls.append(("tiling", tile_rows, level_order))
 
+    def set_partition(self, part_rows=0, cluster_blocks=1):
+        self.calls.append(("partition", part_rows, cluster_blocks))
+
 
 def test_tune_cache_round_trip():
     """The benchmark's tune cache stores the autotuner's choice as JSON and
@@ -95,3 +98,13 @@ def test_tune_cache_round_trip():
         assert p.best_algo == algo and out["algo"] == algo
         assert p.calls[0] == ("tuning", 2, 128, 608)
         assert (("tiling", 512, False) in p.calls) == tiles
+    # the partitioned form: part rows and thread-block cluster size
+    result = {"algo": "partitioned", "best": (1, 512, 0, 0.44, 16384, 4), "per_algo": {}}
+    ch = json.loads(json.dumps(autotune.choice(result)))
+    assert ch == ["partitioned", 1, 512, 0, 16384, 4]
+    p = _FakePlan()
+    autotune.apply_choice(p, ch)
+    assert p.calls == [("tuning", 1, 512, 0), ("partition", 16384, 4)]
+    p = _FakePlan()
+    autotune.apply_choice(p, ["partitioned", 1, 512, 0, 0, False])   # no cluster recorded
+    assert p.calls[-1] == ("partition", 0, 1)
