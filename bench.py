@@ -219,6 +219,8 @@ def main():
     ap.add_argument("--block", type=int, default=256)
     ap.add_argument("--part-rows", type=int, default=0,
                     help="--single-solve: rows per part of the partitioned form (0: automatic)")
+    ap.add_argument("--cluster", type=int, default=1,
+                    help="--single-solve: thread-block cluster size of the partitioned form")
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--extended", action="store_true",
                     help="also measure the general, multi-RHS, batched, refined and autograd "
@@ -564,7 +566,7 @@ def single_solve(args):
     p = TriangularPlan(torch.tensor(A.rowptr, device=dev), torch.tensor(A.colidx, device=dev),
                        torch.tensor(A.vals, device=dev), upper=A.upper, unit=A.unit)
     p.set_tuning(args.lanes, args.block, args.max_blocks)
-    p.set_partition(args.part_rows)
+    p.set_partition(args.part_rows, args.cluster)
     b = torch.tensor(bh, device=dev)
     x = torch.empty_like(b)
     for _ in range(args.repeat):
@@ -573,7 +575,7 @@ def single_solve(args):
     err = float(np.max(np.abs(x.cpu().numpy() - xt)) / np.max(np.abs(xt)))
     print(json.dumps({"single_solve": args.single_solve, "algo": args.algo, "lanes": args.lanes,
                       "block": args.block, "max_blocks": args.max_blocks,
-                      "part_rows": p.partition,
+                      "part_rows": p.partition, "cluster": p.partition_shape[1],
                       "max_rel_err_vs_xtrue": err}))
 
 
