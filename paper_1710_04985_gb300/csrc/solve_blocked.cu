@@ -243,8 +243,23 @@ __global__ void __launch_bounds__(1024) blocked_solve_k1(SolveParams p, int tile
                 if (!lane_done && pend == 0) {
                     sum = fold_chunk(sum, a, v, live);
                     q0 += W * E;
-                    if (q0 >= end) lane_done = true;
-                    else load_chunk();
+                    if (q0 >= end) {
+                        lane_done = true;
+                        // one lane per row: the row is complete, publish it at
+                        // once (no lane reduction to wait for)
+                        if (W == 1 && has_row && i != p.withhold) {
+                            const T xi = publishable(sum);
+                            if (CS > 1)
+                                st_cluster(xs + off, xi);
+                            else
+                                sts_volatile(xs + off, xi);
+                            st_relaxed(xp + k, xi);
+                            x[(long long)i * p.ldx] = xi;
+                            published = true;
+                        }
+                    } else {
+                        load_chunk();
+                    }
                 }
                 const unsigned done = __ballot_sync(FULL, lane_done);
                 const bool fresh = !published && (done & gmask) == gmask;

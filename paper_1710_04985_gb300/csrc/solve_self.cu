@@ -155,8 +155,19 @@ __global__ void __launch_bounds__(1024) self_solve_k1(SolveParams p) {
             if (!lane_done && pend == 0) {  // fold a complete chunk in entry order
                 sum = fold_chunk(sum, a, v, live);
                 q0 += W * E;
-                if (q0 >= end) lane_done = true;
-                else load_chunk();
+                if (q0 >= end) {
+                    lane_done = true;
+                    // one lane per row: the row is complete, publish it at once
+                    // (no lane reduction to wait for)
+                    if (W == 1 && has_row && i != p.withhold) {
+                        const T val = publishable(sum);
+                        st_relaxed(xpub + (PERM ? k : (long long)i * p.ldx), val);
+                        if (PERM) x[(long long)i * p.ldx] = val;
+                        published = true;
+                    }
+                } else {
+                    load_chunk();
+                }
             }
             const unsigned done = __ballot_sync(FULL, lane_done);
             const bool fresh = !published && (done & gmask) == gmask;
