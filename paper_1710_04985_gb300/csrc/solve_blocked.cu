@@ -1,5 +1,6 @@
-// Blocked self-scheduled solve (SPTRSV_ALGO_SELF_BLOCKED), one right-hand
-// side, on the plan's level-ordered copy.
+// Blocked self-scheduled solve, one right-hand side: on the plan's
+// level-ordered copy (SPTRSV_ALGO_SELF_BLOCKED) or, one part per tile, on its
+// part-ordered copy (SPTRSV_ALGO_SELF_PARTITIONED, solve_parts.cu).
 //
 // When levels are narrow (tens to hundreds of rows), a solve is a long chain
 // of small steps and every step of Alg. 3 pays an L2 handshake (~0.6-0.8 us
@@ -25,7 +26,10 @@
 // this block or on earlier tiles held by running blocks.  Every wait is
 // bounded.  Each row is reduced in the same order as in the other
 // self-scheduled forms, so results are bitwise equal for the same sub-warp
-// width.
+// width.  With one lane per row a row is published right after its last
+// fold (no lane reduction to wait for).  Optionally (CS > 1) thread-block
+// clusters of CS blocks take CS consecutive tiles together and read each
+// other's tiles in distributed shared memory.
 #include "internal.h"
 
 namespace sptrsv {

@@ -73,6 +73,10 @@ def test_host_argument_checks_without_gpu(lib):
     assert lib.sptrsv_set_spin_limit(None, 10) == 1
     assert lib.sptrsv_free(None) == 1
     assert lib.sptrsv_reanalyze(None, 0, 1, None) == 1
+    assert lib.sptrsv_set_partition(None, 0, 1) == 1
+    assert lib.sptrsv_set_algo_tuning(None, 1, 4, 256, 0) == 1
+    v = ctypes.c_int()
+    assert lib.sptrsv_get_partition(None, ctypes.byref(v), ctypes.byref(v)) == 1
     assert lib.sptrsv_last_launch_count(None) == 0
 
 
