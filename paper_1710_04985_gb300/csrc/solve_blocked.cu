@@ -238,6 +238,17 @@ __global__ void __launch_bounds__(1024) blocked_solve_k1(SolveParams p, int tile
                 for (int e = 0; e < E; ++e)
                     if ((live & (1u << e)) && Marker<T>::pending(v[e])) pend |= 1u << e;
             };
+            // one lane per row: store the row's value (shared memory, the
+            // publication buffer and x)
+            auto publish_row = [&](T tot) {
+                const T xi = publishable(tot);
+                if (CS > 1)
+                    st_cluster(xs + off, xi);
+                else
+                    sts_volatile(xs + off, xi);
+                st_relaxed(xp + k, xi);
+                x[(long long)i * p.ldx] = xi;
+            };
             bool lane_done = q0 >= end;
             if (!lane_done) load_chunk();
             bool published = !has_row;
@@ -252,13 +263,7 @@ __global__ void __launch_bounds__(1024) blocked_solve_k1(SolveParams p, int tile
                         // one lane per row: the row is complete, publish it at
                         // once (no lane reduction to wait for)
                         if (W == 1 && has_row && i != p.withhold) {
-                            const T xi = publishable(sum);
-                            if (CS > 1)
-                                st_cluster(xs + off, xi);
-                            else
-                                sts_volatile(xs + off, xi);
-                            st_relaxed(xp + k, xi);
-                            x[(long long)i * p.ldx] = xi;
+                            publish_row(sum);
                             published = true;
                         }
                     } else {
@@ -296,6 +301,15 @@ __global__ void __launch_bounds__(1024) blocked_solve_k1(SolveParams p, int tile
                         for (int e = 0; e < E; ++e)
                             if ((pend & (1u << e)) && !Marker<T>::pending(v[e]))
                                 pend &= ~(1u << e);
+                        // one lane per row and this was the row's last chunk:
+                        // fold and publish now, before the warp leaves the wait
+                        if (W == 1 && !lane_done && pend == 0 && q0 + E >= end) {
+                            sum = fold_chunk(sum, a, v, live);
+                            q0 += E;
+                            lane_done = true;
+                            if (has_row && i != p.withhold) publish_row(sum);
+                            published = true;
+                        }
                         if (++waits >= p.spin.limit) {
                             if (pend) {
                                 report(p.status, i, kCodeTimeout);

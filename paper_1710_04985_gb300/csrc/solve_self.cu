@@ -146,6 +146,12 @@ __global__ void __launch_bounds__(1024) self_solve_k1(SolveParams p) {
             for (int e = 0; e < E; ++e)
                 if ((live & (1u << e)) && Marker<T>::pending(v[e])) pend |= 1u << e;
         };
+        // one lane per row: store the row's value (and x, on the copy)
+        auto publish_row = [&](T tot) {
+            const T val = publishable(tot);
+            st_relaxed(xpub + (PERM ? k : (long long)i * p.ldx), val);
+            if (PERM) x[(long long)i * p.ldx] = val;
+        };
         bool lane_done = q0 >= end;
         if (!lane_done) load_chunk();
         bool published = !has_row;
@@ -160,9 +166,7 @@ __global__ void __launch_bounds__(1024) self_solve_k1(SolveParams p) {
                     // one lane per row: the row is complete, publish it at once
                     // (no lane reduction to wait for)
                     if (W == 1 && has_row && i != p.withhold) {
-                        const T val = publishable(sum);
-                        st_relaxed(xpub + (PERM ? k : (long long)i * p.ldx), val);
-                        if (PERM) x[(long long)i * p.ldx] = val;
+                        publish_row(sum);
                         published = true;
                     }
                 } else {
@@ -197,6 +201,15 @@ __global__ void __launch_bounds__(1024) self_solve_k1(SolveParams p) {
 #pragma unroll
                     for (int e = 0; e < E; ++e)
                         if ((pend & (1u << e)) && !Marker<T>::pending(v[e])) pend &= ~(1u << e);
+                    // one lane per row and this was the row's last chunk: fold
+                    // and publish now, before the warp leaves the wait
+                    if (W == 1 && !lane_done && pend == 0 && q0 + E >= end) {
+                        sum = fold_chunk(sum, a, v, live);
+                        q0 += E;
+                        lane_done = true;
+                        if (has_row && i != p.withhold) publish_row(sum);
+                        published = true;
+                    }
                     if (++waits >= p.spin.limit) {
                         if (pend) {
                             report(p.status, i, kCodeTimeout);
