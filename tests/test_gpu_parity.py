@@ -530,6 +530,31 @@ def test_timeout_is_reported_and_solve_finishes(algo):
         assert p.status() == (0, -1)
 
 
+@pytest.mark.parametrize("cluster", [1, 2, 4])
+@pytest.mark.parametrize("withheld", [300, 293])
+def test_partitioned_timeout_in_part_and_across_the_cluster(cluster, withheld):
+    """Bidiagonal chain, parts of 14 rows: row 300's dependent waits inside
+    its part (shared memory), row 293's dependent (row 294, first row of the
+    next part) waits in the previous block's shared memory when both parts
+    belong to one cluster, else in L2.  Every such wait gives up after the
+    spin limit with SPTRSV_ERR_TIMEOUT; the next solve is clean."""
+    A = bidiagonal(2000)
+    b = synth.uniform(A.n, 29)
+    ref = oracle.solve(A.rowptr, A.colidx, A.vals, b)
+    with plan_for(A) as p:
+        p.set_partition(14, cluster)
+        p.set_tuning(1, 128, 0)
+        p.set_spin_limit(1 << 14)
+        p.withhold_row(withheld)
+        x = p.solve(torch.tensor(b, device=dev()), algo="partitioned").cpu().numpy()
+        assert p.status() == (6, withheld + 1)
+        assert relerr(x[:withheld], ref[:withheld]) <= TOL64
+        assert np.all(np.isnan(x[withheld + 1:]))
+        p.withhold_row(-1)
+        assert relerr(p.solve(torch.tensor(b, device=dev()), algo="partitioned"), ref) <= TOL64
+        assert p.status() == (0, -1)
+
+
 # ---------------------------------------------------------------- gradient / residual
 
 @pytest.mark.parametrize("name", ["general", "ilu_L", "ilu_U", "unit_nodiag"])
