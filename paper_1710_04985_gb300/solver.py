@@ -143,7 +143,13 @@ class TriangularPlan:
         return out
 
     def solve(self, b, out=None, algo="self", stream=None):
-        """x = A^{-1} b (forward or backward substitution, Sec. 3.1)."""
+        """x = A^{-1} b (forward or backward substitution, Sec. 3.1).
+
+        algo: "self" (Alg. 3, in place), "permuted" (on the level-ordered
+        copy), "blocked" (tiles of that copy), "partitioned" (parts of
+        consecutive rows, on the part-ordered copy), "tiled", "chains",
+        "column" (Alg. 4), "level" (Alg. 1) or "auto" (the autotuner's
+        choice, ``best_algo``)."""
         return self._solve(_lib.load().sptrsv_solve, "sptrsv_solve", b, out, algo, stream)
 
     def solve_transpose(self, b, out=None, algo="self", stream=None):
