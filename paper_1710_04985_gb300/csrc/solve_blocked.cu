@@ -321,7 +321,16 @@ __global__ void __launch_bounds__(1024) blocked_solve_k1(SolveParams p, int tile
                             waits = 0;
                             break;
                         }
-                        if (__any_sync(FULL, pend != before)) break;
+                        if (W == 1) {
+                            // rows of one lane publish inside the loop: leave it
+                            // only when every lane is done or one needs its next
+                            // chunk (one warp reduction per round)
+                            const unsigned w = __reduce_or_sync(
+                                FULL, lane_done ? 0u : (pend != 0 ? 1u : 2u));
+                            if ((w & 2u) || !(w & 1u)) break;
+                        } else if (__any_sync(FULL, pend != before)) {
+                            break;
+                        }
                         if (waits >= p.spin.hot &&
                             __any_sync(FULL, (pend & ~local & ~remote) != 0)) {
                             __nanosleep(ns);  // back off only while an L2 dependency is pending

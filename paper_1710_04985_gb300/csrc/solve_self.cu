@@ -221,7 +221,15 @@ __global__ void __launch_bounds__(1024) self_solve_k1(SolveParams p) {
                         waits = 0;
                         break;
                     }
-                    if (__any_sync(FULL, pend != before)) break;  // something arrived
+                    if (W == 1) {
+                        // rows of one lane publish inside the loop: leave it only
+                        // when every lane is done or one needs its next chunk
+                        const unsigned w = __reduce_or_sync(
+                            FULL, lane_done ? 0u : (pend != 0 ? 1u : 2u));
+                        if ((w & 2u) || !(w & 1u)) break;
+                    } else if (__any_sync(FULL, pend != before)) {
+                        break;  // something arrived
+                    }
                     if (waits >= p.spin.hot) {
                         __nanosleep(ns);
                         ns = ns < p.spin.max_ns ? ns * 2 : p.spin.max_ns;
