@@ -108,3 +108,77 @@ def test_tune_cache_round_trip():
     p = _FakePlan()
     autotune.apply_choice(p, ["partitioned", 1, 512, 0, 0, False])   # no cluster recorded
     assert p.calls[-1] == ("partition", 0, 1)
+
+
+class _ModelPlan(_FakePlan):
+    """A plan whose solve time is a fixed function of its launch shape, for
+    checking the autotuner's search and bookkeeping without a GPU."""
+
+    class _Ptr:
+        def __init__(self, v):
+            self.v = v
+
+        def data_ptr(self):
+            return self.v
+
+    def __init__(self):
+        super().__init__()
+        import torch
+        self.n, self.nnz, self.upper, self.unit, self.dtype = 1000, 4000, False, False, torch.float64
+        self.rowptr, self.colidx = self._Ptr(1), self._Ptr(2)
+        self.shape = (4, 256, 0)
+        self.part = (0, 1)
+        self.algo_shapes = {}
+
+    def set_tuning(self, lanes, block, max_blocks):
+        super().set_tuning(lanes, block, max_blocks)
+        self.shape = (lanes, block, max_blocks)
+        self.algo_shapes = {}
+
+    def set_partition(self, part_rows=0, cluster_blocks=1):
+        super().set_partition(part_rows, cluster_blocks)
+        self.part = (part_rows, cluster_blocks)
+
+    def set_algo_tuning(self, algo, lanes, block, max_blocks):
+        self.algo_shapes[algo] = (lanes, block, max_blocks)
+
+    def model_ms(self, algo):
+        lanes, block, _ = self.shape
+        base = {"self": 1.0, "permuted": 0.9, "partitioned": 0.8}.get(algo, 2.0)
+        if algo == "partitioned":
+            rows, cl = self.part
+            base += (0.0 if rows == 16384 else 0.1) - (0.05 if cl == 4 else 0.0)
+            return base + (0.0 if lanes == 1 else 0.2) + (0.0 if block == 512 else 0.03)
+        return base + (0.0 if lanes == 2 else 0.2) + (0.0 if block == 128 else 0.03)
+
+
+def test_autotuner_search_and_per_form_shapes(monkeypatch):
+    """tune_algos keeps the fastest form, applies its shape (for the
+    partitioned form: part size and cluster size too), and records every
+    measured form's own best shape on the plan."""
+    import types
+
+    import torch
+
+    from paper_1710_04985_gb300 import autotune
+    monkeypatch.setattr(torch.cuda, "get_device_properties",
+                        lambda dev: types.SimpleNamespace(multi_processor_count=152))
+    monkeypatch.setattr(autotune, "time_solve",
+                        lambda plan, b, x, algo="self", reps=3, transpose=False:
+                        plan.model_ms(algo))
+    p = _ModelPlan()
+    b = torch.zeros(1000, dtype=torch.float64)
+    res = autotune.tune_algos(p, b, torch.empty_like(b), use_cache=False,
+                              algos=("self", "permuted", "partitioned"))
+    assert res["algo"] == "partitioned" and p.best_algo == "partitioned"
+    lanes, block, max_blocks, ms, rows, cluster = res["best"]
+    assert (lanes, block, rows, cluster) == (1, 512, 16384, 4)
+    assert abs(ms - 0.75) < 1e-12
+    assert p.part == (16384, 4)
+    # every form keeps its own best shape; the in-place and level-ordered forms
+    # prefer 2 lanes and 128 threads in this model
+    assert p.algo_shapes["partitioned"][:2] == (1, 512)
+    assert p.algo_shapes["self"][:2] == (2, 128)
+    assert p.algo_shapes["permuted"][:2] == (2, 128)
+    # the cluster stage ran for the partitioned form only
+    assert ("partition", 16384, 2) in p.calls and ("partition", 16384, 4) in p.calls
