@@ -182,3 +182,15 @@ def test_autotuner_search_and_per_form_shapes(monkeypatch):
     assert p.algo_shapes["permuted"][:2] == (2, 128)
     # the cluster stage ran for the partitioned form only
     assert ("partition", 16384, 2) in p.calls and ("partition", 16384, 4) in p.calls
+
+
+def test_bench_tuning_row_reports_parts_and_clusters():
+    import bench
+    assert bench._tuning_row({"algo": "partitioned", "best": (1, 512, 0, 0.4, 16384, 4)}) == \
+        [1, 512, 0, 16384, 4]
+    assert bench._tuning_row({"algo": "partitioned", "best": (1, 512, 0, 0.4, 0, False)}) == \
+        [1, 512, 0, 0, 1]
+    assert bench._tuning_row({"algo": "tiled", "best": (4, 256, 0, 0.4, 2048, True)}) == \
+        [4, 256, 0, 2048, True]
+    assert bench._tuning_row({"algo": "permuted", "best": (2, 128, 608, 0.4, 2048, False)}) == \
+        [2, 128, 608, None, None]
