@@ -25,7 +25,8 @@ def w2(cuda_device):
 
 def bench_plan(A, b, dtype=torch.float64):
     """The plan as the benchmark builds it: analysed, then autotuned over the
-    level-ordered and tiled self-scheduled forms."""
+    self-scheduled forms (in place, level-ordered copy, blocked, partitioned,
+    tiled, chained); each form keeps its own tuned launch shape."""
     from paper_1710_04985_gb300 import autotune
     p = plan_for(A, dtype)
     autotune.tune_algos(p, torch.tensor(b, device=dev(), dtype=dtype))
@@ -41,7 +42,7 @@ def test_workload1_ilu_factors_forward_and_backward(w1):
             assert_levels_equal(p.levels(), A)
             assert p.levels()["nlev"] == 382
             bt = torch.tensor(b, device=dev())
-            for algo in ("auto", "self", "permuted", "tiled", "level"):
+            for algo in ("auto", "self", "permuted", "partitioned", "tiled", "level"):
                 assert relerr(p.solve(bt, algo=algo), ref) <= TOL64
             assert relerr(ref, xt) <= 1e-10           # manufactured solution recovered
             assert p.status() == (0, -1)
