@@ -112,11 +112,14 @@ typedef enum {
                                      (allocates ~12 B per entry + 12 B per row in FP64,
                                      synchronises the stream, refused with
                                      SPTRSV_ERR_NOT_SUPPORTED during graph capture).
-                                     The copy is a SNAPSHOT of the values: after
-                                     changing d_vals in place call
-                                     sptrsv_refresh_values (sptrsv_set_values does it).
-                                     One right-hand side; more columns fall back to
-                                     SPTRSV_ALGO_SELF                                    */,
+                                     The copy is a SNAPSHOT of the values (pre-scaled
+                                     by 1/d(i) for a non-unit matrix): after changing
+                                     d_vals in place call sptrsv_refresh_values
+                                     (sptrsv_set_values does it).  More right-hand
+                                     sides run the multi-RHS kernel on the same copy,
+                                     with a position-ordered [n][nrhs] publication
+                                     buffer (allocated on first use of each larger
+                                     nrhs)                                               */,
     SPTRSV_ALGO_SELF_COLUMN = 5   /* Alg. 4 (SLFC): column-wise self-scheduled solve.
                                      Unknowns in level order wait on a dependency
                                      counter, then push a(r,i) x(i) into every
@@ -140,25 +143,32 @@ typedef enum {
                                      memory, warps take row groups dynamically, the
                                      tile's rows are prefetched into L2.  For narrow
                                      levels.  Bitwise equal to SPTRSV_ALGO_SELF for
-                                     equal lanes.  One right-hand side; more columns
-                                     fall back to SPTRSV_ALGO_SELF                       */,
+                                     equal lanes.  More right-hand sides run as with
+                                     SPTRSV_ALGO_SELF_PERMUTED                           */,
     SPTRSV_ALGO_SELF_PARTITIONED = 7  /* the blocked solve of SPTRSV_ALGO_SELF_BLOCKED
-                                     on a part-ordered copy: the rows are cut into
-                                     parts of part_rows consecutive rows in order of
-                                     substitution (sptrsv_set_partition), listed part
-                                     after part and by level (Sec. 4.1) inside a part,
-                                     and a thread block takes one part per tile, so a
-                                     dependency inside the part passes through shared
-                                     memory and only dependencies on earlier parts
-                                     wait on published values in L2 (Alg. 3).  On a
-                                     grid in natural order a part is a slab of grid
-                                     lines.  Built on first use (a copy of the pattern
-                                     and values, same value snapshot as
+                                     on a part-ordered copy: the substitution order is
+                                     split where the matrix decouples (every system
+                                     boundary of a block-diagonal batch), long blocks
+                                     are cut into parts of at most part_rows
+                                     consecutive rows (sptrsv_set_partition), short
+                                     ones packed together; parts are listed in the
+                                     order they are handed out (see
+                                     sptrsv_partition_info) and by level (Sec. 4.1)
+                                     inside a part, and a thread block takes one part
+                                     per tile, so a dependency inside the part passes
+                                     through shared memory and only dependencies on
+                                     earlier parts wait on published values in L2
+                                     (Alg. 3).  On a grid in natural order a part is a
+                                     slab of grid lines.  Built on first use (a copy of
+                                     the pattern and values, same value snapshot as
                                      SPTRSV_ALGO_SELF_PERMUTED, allocates and
                                      synchronises; not during graph capture) and again
                                      when the part size changes.  Bitwise equal to
-                                     SPTRSV_ALGO_SELF for equal lanes.  One right-hand
-                                     side; more columns fall back to SPTRSV_ALGO_SELF   */
+                                     SPTRSV_ALGO_SELF for equal lanes.  More right-hand
+                                     sides run as with SPTRSV_ALGO_SELF_PERMUTED         */,
+    SPTRSV_ALGO_AUTO = 8          /* the plan's default form (sptrsv_set_default_algo;
+                                     SPTRSV_ALGO_SELF until one is set), e.g. the one an
+                                     autotuner measured fastest                          */
 } sptrsv_algo_t;
 
 /* Level-analysis methods (sptrsv_reanalyze).  All give the same levels and
@@ -230,7 +240,11 @@ SPTRSV_API sptrsv_status_t sptrsv_free(sptrsv_plan_t plan);
 
 /* Solves op(A) x = b with op = identity: forward substitution for a lower
  * plan, backward for an upper one (Sec. 3.1), by Alg. 1 (SPTRSV_ALGO_LEVEL)
- * or Alg. 3 (SPTRSV_ALGO_SELF and its tiled and chained forms).
+ * or Alg. 3 (SPTRSV_ALGO_SELF and its other forms).  The level-ordered,
+ * blocked and partitioned forms solve from the plan's SNAPSHOT of the values
+ * (a copy made on first use): after changing d_vals in place call
+ * sptrsv_refresh_values before solving again; the other forms read d_vals
+ * at every solve.
  *   d_b, d_x  device [n][ld], element type of the plan, nrhs >= 1 columns
  *   ld        leading dimension of both, ld >= nrhs
  * With the self-scheduled algorithms, x is overwritten with a "not yet solved" marker
@@ -257,6 +271,17 @@ SPTRSV_API sptrsv_status_t sptrsv_solve_transpose(sptrsv_plan_t plan, const void
  * sptrsv_solve_transpose); synchronises `stream`. */
 SPTRSV_API sptrsv_status_t sptrsv_prepare_transpose(sptrsv_plan_t plan, void *stream);
 
+/* Builds now whatever the first solve of `algo` (SPTRSV_ALGO_AUTO: the
+ * plan's default form) in the forward (transpose = 0) or transposed
+ * (transpose = 1) direction would build on first use: the transposed pattern
+ * and its levels, the level- or part-ordered copy, the segment order of the
+ * chained form or the counters of the column-wise form.  Allocates and
+ * synchronises `stream` (refused with SPTRSV_ERR_NOT_SUPPORTED during
+ * capture), so that later solves can be captured in a CUDA graph, and so
+ * that this part of the setup (Sec. 4.4) can be timed on its own. */
+SPTRSV_API sptrsv_status_t sptrsv_prepare(sptrsv_plan_t plan, int transpose,
+                                          sptrsv_algo_t algo, void *stream);
+
 /* ------------------------------------------------------- differentiation */
 
 /* Gradient of a loss through x = A^{-1} b with respect to the stored values:
@@ -280,21 +305,32 @@ SPTRSV_API sptrsv_status_t sptrsv_residual(sptrsv_plan_t plan, const double *d_b
 
 /* Mixed-precision solve with iterative refinement (F64 plans only; the
  * motivation is the refinement use of Sec. 1).  The bulk triangular solves
- * run in FP32 (an FP32 copy of the values, FP32 vectors and accumulation);
- * the residual r = b - A x, the correction update x += d and the solution
- * are FP64.  Stops when max|r| / (max|b| + ||A||_inf max|x|) <= tol or after
- * max_iter corrections.
+ * run in FP32 (an FP32 copy of the values, FP32 vectors and accumulation)
+ * with the plan's default form (sptrsv_set_default_algo) and that form's
+ * launch shape; the residual r = b - A x, the correction update x += d and
+ * the solution are FP64.  The in-place, level-ordered, blocked and
+ * partitioned forms add every correction into x as they publish it (no
+ * separate update pass); each residual pass also writes the FP32 right-hand
+ * side of the next correction.  Stops when
+ * max|r| / (max|b| + ||A||_inf max|x|) <= tol or after max_iter corrections.
  *   d_b, d_x     device FP64 [n][ld]; x is overwritten (no initial guess)
  *   iters        out (nullable): corrections applied after the first solve
  *   rel_resid    out (nullable): the last relative residual measured
  * Synchronises `stream` once per iteration to read the residual norm; the
- * first call allocates the FP32 copy and scratch.  Not graph capturable.
- * Refresh the FP32 copy after changing the values with
+ * first call allocates the FP32 copy of the values, FP32 copies of the
+ * level- or part-ordered copy its form uses, and scratch.  Not graph
+ * capturable.  Refresh the FP32 copies after changing the values with
  * sptrsv_refresh_values. */
 SPTRSV_API sptrsv_status_t sptrsv_solve_refined(sptrsv_plan_t plan, const double *d_b,
                                      double *d_x, int nrhs, int ld,
                                      int max_iter, double tol, int *iters,
                                      double *rel_resid, void *stream);
+
+/* The form SPTRSV_ALGO_AUTO and the FP32 solves of sptrsv_solve_refined
+ * run (any algorithm but SPTRSV_ALGO_AUTO; SPTRSV_ALGO_SELF by default).
+ * The getter returns it as an int. */
+SPTRSV_API sptrsv_status_t sptrsv_set_default_algo(sptrsv_plan_t plan, sptrsv_algo_t algo);
+SPTRSV_API sptrsv_status_t sptrsv_get_default_algo(sptrsv_plan_t plan, int *algo);
 
 /* Points the plan at a new values array with the same pattern and element
  * type (for example a new parameter tensor); borrowed like the first one.
@@ -304,9 +340,13 @@ SPTRSV_API sptrsv_status_t sptrsv_solve_refined(sptrsv_plan_t plan, const double
 SPTRSV_API sptrsv_status_t sptrsv_set_values(sptrsv_plan_t plan, const void *d_vals,
                                              void *stream);
 
-/* Re-reads d_vals into the plan's copies of the values, if they exist: the
- * FP32 copy of sptrsv_solve_refined and the level-ordered copies of
- * SPTRSV_ALGO_SELF_PERMUTED.  Async. */
+/* Re-reads d_vals into every copy of the values the plan holds: the FP32
+ * copy of sptrsv_solve_refined, the level-ordered copy of
+ * SPTRSV_ALGO_SELF_PERMUTED / _BLOCKED (and of their multi-RHS solves), the
+ * part-ordered copy of SPTRSV_ALGO_SELF_PARTITIONED, and the FP32 versions of
+ * both copies that refined solves use.  Solves of those forms read the copies,
+ * not d_vals: after changing d_vals in place, call this (on the solves'
+ * stream, or synchronise) before the next solve.  Async. */
 SPTRSV_API sptrsv_status_t sptrsv_refresh_values(sptrsv_plan_t plan, void *stream);
 
 /* ----------------------------------------------------------------- tuning */
@@ -374,6 +414,27 @@ SPTRSV_API sptrsv_status_t sptrsv_set_partition(sptrsv_plan_t plan, int part_row
 SPTRSV_API sptrsv_status_t sptrsv_get_partition(sptrsv_plan_t plan, int *part_rows,
                                                 int *cluster_blocks);
 
+/* Layout of the part-ordered copy of the forward (transpose = 0) or
+ * transposed (transpose = 1) system, as the last partitioned solve in that
+ * direction built it (SPTRSV_ERR_NOT_SUPPORTED before the first).  The
+ * substitution order is split where the matrix decouples (no row at or after
+ * a position depends on a row before it; a block-diagonal batch decouples at
+ * every system boundary) into *nblocks independent blocks; a block longer
+ * than half the part size is cut into balanced parts of at most part_rows
+ * rows, shorter neighbouring blocks share a part; the *nparts parts are
+ * handed out to thread blocks deepest block first (its level count, Sec.
+ * 4.1), in order of substitution among equals.  *max_part_rows is the
+ * longest part.  All outputs nullable; the device arrays are owned by the
+ * plan and valid until the copy is rebuilt or the plan freed:
+ *   d_part_ptr  int[nparts + 1]: first position of each part, in hand-out
+ *               order (position k of the copy holds row d_order[k])
+ *   d_order     int[n]: the row at each position of the copy */
+SPTRSV_API sptrsv_status_t sptrsv_partition_info(sptrsv_plan_t plan, int transpose,
+                                                 int *nparts, int *nblocks,
+                                                 int *max_part_rows,
+                                                 const int **d_part_ptr,
+                                                 const int **d_order);
+
 /* Upper bound on the polling rounds of one dependency wait before the wait
  * gives up, records SPTRSV_ERR_TIMEOUT with its row and goes on with NaN so
  * that every later row still finishes.  Default 2^24 rounds (several
@@ -435,7 +496,12 @@ SPTRSV_API int sptrsv_last_launch_count(sptrsv_plan_t plan);
 
 /* Largest n that sptrsv_solve_noalloc accepts.  Its working memory is one
  * fixed array inside the library: 256 bytes plus 4 bytes per row, i.e.
- * 16 MiB + 256 B, held on every GPU that loads the library until exit. */
+ * 16 MiB + 256 B per GPU.  With CUDA's lazy module loading (the default
+ * since CUDA 12) the array is reserved on a device when the library's code
+ * is first used there, often by the first sptrsv_solve_noalloc call, and
+ * then held until the process exits.  A caller whose own pool takes all
+ * device memory should make one warm-up call per device before the pool
+ * claims it (and before any stream capture, see below). */
 #define SPTRSV_NOALLOC_MAX_ROWS 4194304
 
 /* Solves A x = b for one right-hand side without a plan and without any
@@ -451,11 +517,15 @@ SPTRSV_API int sptrsv_last_launch_count(sptrsv_plan_t plan);
  * in substitution order (rows wait for per-row ready flags; no level sets).
  *   n, nnz, d_rowptr, d_colidx, d_vals, dtype, uplo, diag: as sptrsv_analyze
  *   d_b, d_x   device vectors of n elements, contiguous; d_x == d_b allowed
- *   error_row  NULL: return right after enqueueing (device-side errors are
- *              then not reported).  Non-NULL: wait for `stream`, then return
- *              the device-side result -- SPTRSV_ERR_STRUCTURE or
- *              SPTRSV_ERR_ZERO_PIVOT from validation (x untouched) or
- *              SPTRSV_ERR_TIMEOUT -- with its row in *error_row (-1 if none).
+ *   error_row  NULL: return right after enqueueing; SPTRSV_OK then only
+ *              means "enqueued", and device-side errors are not reported.
+ *              Non-NULL: wait for `stream`, then return the device-side
+ *              result -- SPTRSV_ERR_STRUCTURE or SPTRSV_ERR_ZERO_PIVOT from
+ *              validation (x untouched) or SPTRSV_ERR_TIMEOUT -- with its
+ *              row in *error_row (-1 if none).
+ * A dependency wait gives up after SPTRSV_SPIN_LIMIT polls (environment
+ * variable, read at every call; 2^24 by default), reports
+ * SPTRSV_ERR_TIMEOUT for its row and goes on with NaN.
  * Returns SPTRSV_ERR_INVALID_ARG for n > SPTRSV_NOALLOC_MAX_ROWS.
  * Working memory: one array declared at file scope in the library, shared by
  * every call; each call clears the parts it uses before reading them, and

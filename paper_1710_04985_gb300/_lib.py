@@ -26,7 +26,7 @@ F64, F32 = 0, 1
 LOWER, UPPER = 0, 1
 NON_UNIT, UNIT = 0, 1
 (ALGO_LEVEL, ALGO_SELF, ALGO_SELF_TILED, ALGO_SELF_CHAINS, ALGO_SELF_PERMUTED,
- ALGO_SELF_COLUMN, ALGO_SELF_BLOCKED, ALGO_SELF_PARTITIONED) = 0, 1, 2, 3, 4, 5, 6, 7
+ ALGO_SELF_COLUMN, ALGO_SELF_BLOCKED, ALGO_SELF_PARTITIONED, ALGO_AUTO) = 0, 1, 2, 3, 4, 5, 6, 7, 8
 
 # (name, restype, argtypes) for every entry point of include/sptrsv.h
 _c_int, _c_ll, _c_dbl = ctypes.c_int, ctypes.c_longlong, ctypes.c_double
@@ -41,9 +41,12 @@ SIGNATURES = [
     ("sptrsv_solve", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _c_int, _vp]),
     ("sptrsv_solve_transpose", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _c_int, _vp]),
     ("sptrsv_prepare_transpose", _c_int, [_vp, _vp]),
+    ("sptrsv_prepare", _c_int, [_vp, _c_int, _c_int, _vp]),
     ("sptrsv_grad_vals", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _vp, _vp]),
     ("sptrsv_residual", _c_int, [_vp, _vp, _vp, _vp, _c_int, _c_int, _vp]),
     ("sptrsv_solve_refined", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _c_int, _c_dbl, _ip, _dp, _vp]),
+    ("sptrsv_set_default_algo", _c_int, [_vp, _c_int]),
+    ("sptrsv_get_default_algo", _c_int, [_vp, _ip]),
     ("sptrsv_set_values", _c_int, [_vp, _vp, _vp]),
     ("sptrsv_refresh_values", _c_int, [_vp, _vp]),
     ("sptrsv_set_tuning", _c_int, [_vp, _c_int, _c_int, _c_int]),
@@ -54,6 +57,7 @@ SIGNATURES = [
     ("sptrsv_set_tiling", _c_int, [_vp, _c_int, _c_int]),
     ("sptrsv_set_partition", _c_int, [_vp, _c_int, _c_int]),
     ("sptrsv_get_partition", _c_int, [_vp, _ip, _ip]),
+    ("sptrsv_partition_info", _c_int, [_vp, _c_int, _ip, _ip, _ip, _pp, _pp]),
     ("sptrsv_levels", _c_int, [_vp, _c_int, _ip, _pp, _pp, _pp]),
     ("sptrsv_transpose_pattern", _c_int, [_vp, _pp, _pp, _pp]),
     ("sptrsv_status", _c_int, [_vp, _vp, _ip]),

@@ -62,7 +62,7 @@ def tune(plan, b, x=None, algo="self", lanes=LANES, blocks=BLOCKS, grids=GRID_FR
     partitioned form tile_rows is the part size and the last field the
     thread-block cluster size)."""
     nrhs = 1 if b.dim() == 1 else b.shape[1]
-    mrhs = nrhs > 1 and algo in ("self", "level")
+    mrhs = nrhs > 1 and algo in ("self", "level", "permuted")
     if mrhs:
         # multi-RHS solves: the width is the multi-RHS one (4..32 lanes); one
         # lane per column at most
@@ -130,7 +130,7 @@ def tune(plan, b, x=None, algo="self", lanes=LANES, blocks=BLOCKS, grids=GRID_FR
 def _apply(plan, best, algo, nrhs=1):
     """Set a tuning row on the plan: (lanes, block, max_blocks, ms, tile,
     level_order), lanes being the multi-RHS width when nrhs > 1."""
-    if nrhs > 1 and algo in ("self", "level"):
+    if nrhs > 1 and algo in ("self", "level", "permuted"):
         plan.set_mrhs_tuning(best[0], best[1], best[2])
     else:
         plan.set_tuning(best[0], best[1], best[2])
@@ -140,19 +140,39 @@ def _apply(plan, best, algo, nrhs=1):
         plan.set_tiling(best[4], best[5])
 
 
+# A small search per form (``tune_algos(..., quick=True)``): the shapes that
+# won on the stencil factors, the general matrices and the batches measured
+# so far, a few candidates each, for callers that tune several workloads in
+# one short run.
+QUICK = {
+    "self": dict(lanes=(1, 2, 4, 8), blocks=(256,), grids=(0, 2)),
+    "permuted": dict(lanes=(1, 2, 4), blocks=(256, 512), grids=(0,)),
+    "blocked": dict(lanes=(1, 4), blocks=(512, 1024), grids=(0,), tiles=(256, 2048)),
+    "partitioned": dict(lanes=(1, 2, 4), blocks=(256, 512), grids=(0,), tiles=(0, 8192, 16384),
+                        clusters=(4,)),
+    "tiled": dict(lanes=(1, 4), blocks=(256,), grids=(0,), tiles=(2048,), tile_orders=(False,)),
+    "chains": dict(lanes=(2, 4, 8), blocks=(256,), grids=(0,)),
+}
+
+
 def tune_algos(plan, b, x=None, algos=("self", "permuted", "blocked", "partitioned", "tiled",
-                                        "chains"), reps=3, use_cache=True, **kw):
+                                        "chains"), reps=3, use_cache=True, quick=False, **kw):
     """Tune each self-scheduled form and keep the faster one.
 
     Returns ``{"algo": name, "best": ..., "per_algo": {name: tune(...)}}`` and
-    sets ``plan.best_algo`` (used by ``plan.solve(..., algo="auto")``)."""
+    sets ``plan.best_algo`` (used by ``plan.solve(..., algo="auto")`` and by
+    the FP32 solves of ``plan.solve_refined``).  ``quick``: the small
+    per-form searches of ``QUICK``."""
     nrhs = 1 if b.dim() == 1 else b.shape[1]
     if nrhs > 1:
-        algos = tuple(a for a in algos if a not in
-                      ("tiled", "chains", "permuted", "blocked", "partitioned")) or ("self",)
+        # multi-RHS solves run in place or on the level-ordered copy (the
+        # blocked and partitioned forms use that copy too for nrhs > 1)
+        algos = tuple(a for a in algos if a in ("self", "permuted")) or ("self",)
     per = {}
     for a in algos:
-        if a == "tiled" and not kw:
+        if quick and not kw and nrhs == 1:
+            per[a] = tune(plan, b, x, algo=a, reps=reps, use_cache=use_cache, **QUICK[a])
+        elif a == "tiled" and not kw:
             # a lighter search: the tiled form wins only on chain-like matrices
             per[a] = tune(plan, b, x, algo=a, reps=reps, use_cache=use_cache, lanes=(1, 4, 16),
                           blocks=(256, 512), grids=(0, 2), tiles=(512, 2048))
@@ -170,10 +190,12 @@ def tune_algos(plan, b, x=None, algos=("self", "permuted", "blocked", "partition
             per[a] = tune(plan, b, x, algo=a, reps=reps, use_cache=use_cache, **kw)
     name = min(per, key=lambda a: per[a]["best"][3])
     _apply(plan, per[name]["best"], name, nrhs)
-    if nrhs == 1:  # multi-RHS solves always run the in-place kernel
+    if nrhs > 1:   # the multi-RHS form of algo="auto"
+        plan.best_algo_mrhs = name
+    else:
         plan.best_algo = name
         # every measured form keeps its own best shape (the FP32 solves of a
-        # refined solve run the in-place form whichever form won)
+        # refined solve run the winning form, in its shape)
         for a, r in per.items():
             plan.set_algo_tuning(a, *r["best"][:3])
     return {"algo": name, "best": per[name]["best"], "per_algo": per}

@@ -5,7 +5,13 @@ block-diagonal CSR, analysed once, tuned by the autotuner, and solved by one
 persistent self-scheduled launch that a CUDA graph replays.  Rows of
 different systems never wait on one another, so the level sets of the batch
 are the union of the per-system level sets and the launch overlaps the
-systems' dependency chains.
+systems' dependency chains.  The partitioned form finds the system
+boundaries itself (the matrix decouples there): its parts never mix a piece
+of one system with another, and the deepest systems are started first.
+
+``solve_refined`` solves the same batch with FP32 bulk solves and FP64
+iterative refinement (the precision form), one refinement loop for all
+systems together.
 """
 from __future__ import annotations
 
@@ -83,6 +89,15 @@ class BatchedTriangularSolve:
             self.capture()
         self.graph.replay()
         return self.x
+
+    def solve_refined(self, b=None, max_iter=10, tol=8 * 2.0 ** -52):
+        """Every system by FP32 solves (the tuned form) with FP64 residuals
+        and updates; returns ``(x, corrections, relative_residual)``.  FP64
+        batches only; not captured in a graph (each refinement step reads
+        the residual norm on the host)."""
+        if b is not None:
+            self.b.copy_(b)
+        return self.plan.solve_refined(self.b, out=self.x, max_iter=max_iter, tol=tol)
 
     def split(self, x=None):
         x = self.x if x is None else x

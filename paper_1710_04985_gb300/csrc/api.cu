@@ -62,6 +62,9 @@ struct Levels {
     // in parts of qS consecutive rows, by level inside a part; columns
     // renumbered to positions (qipos); xq is the publication buffer of its
     // solves (position order).
+    // qpart: first position of each part (qnparts + 1 entries, parts in the
+    // order they are handed out), qmaxpart the longest part, qnblocks the
+    // independent blocks the substitution order splits into.
     int qS = 0;
     int* qord = nullptr;
     int* qipos = nullptr;
@@ -69,6 +72,19 @@ struct Levels {
     int* qidx = nullptr;
     void* qvals = nullptr;
     void* xq = nullptr;
+    int* qpart = nullptr;
+    int qnparts = 0, qmaxpart = 0, qnblocks = 0;
+    // FP32 values and publication buffers of the level- and part-ordered
+    // copies of an F64 plan, for the FP32 solves of the refined solve (built
+    // on first use from the plan's FP32 copy of the values).
+    void* pvals32 = nullptr;
+    void* xp32 = nullptr;
+    void* qvals32 = nullptr;
+    void* xq32 = nullptr;
+    // multi-RHS solves on the level-ordered copy: publication buffer
+    // [n][nrhs] in position order (grown on demand)
+    void* xpm = nullptr;
+    size_t xpm_bytes = 0;
 };
 
 void free_parts(Levels& L) {
@@ -78,9 +94,12 @@ void free_parts(Levels& L) {
     cudaFree(L.qidx);
     cudaFree(L.qvals);
     cudaFree(L.xq);
-    L.qord = L.qipos = L.qptr = L.qidx = nullptr;
-    L.qvals = L.xq = nullptr;
-    L.qS = 0;
+    cudaFree(L.qpart);
+    cudaFree(L.qvals32);
+    cudaFree(L.xq32);
+    L.qord = L.qipos = L.qptr = L.qidx = L.qpart = nullptr;
+    L.qvals = L.xq = L.qvals32 = L.xq32 = nullptr;
+    L.qS = L.qnparts = L.qmaxpart = L.qnblocks = 0;
 }
 
 struct DeviceGuard {
@@ -176,6 +195,7 @@ struct sptrsv_plan_s {
     bool tile_level_order = false;
     int part_rows = 0;   // partitioned solve: rows per part (0: automatic)
     int part_cluster = 1;  // partitioned solve: blocks per thread-block cluster
+    sptrsv_algo_t default_algo = SPTRSV_ALGO_SELF;  // SPTRSV_ALGO_AUTO and refined solves
     int smem_optin = 0;  // shared memory a block may opt in to
     SpinPolicy spin{1ll << 24, 256, 128};
     int withhold = -1;
@@ -198,6 +218,9 @@ void free_levels(Levels& L) {
     cudaFree(L.pidx);
     cudaFree(L.pvals);
     cudaFree(L.xp);
+    cudaFree(L.pvals32);
+    cudaFree(L.xp32);
+    cudaFree(L.xpm);
     cudaFree(L.count0);
     cudaFree(L.count);
     free_parts(L);
@@ -573,6 +596,14 @@ sptrsv_status_t build_chain(sptrsv_plan_t P, bool trans, int lanes, cudaStream_t
     return SPTRSV_OK;
 }
 
+// How the copies store a row's values: pre-scaled by 1/d(i) with the
+// diagonal's slot at the row's start (1) or end (0) for a non-unit matrix,
+// as they are (-1) for a unit one.
+int copy_diag(sptrsv_plan_t P, bool trans) {
+    if (P->unit) return -1;
+    return (trans ? !P->upper : P->upper) ? 1 : 0;
+}
+
 // Level-ordered copy of one direction's pattern and values (Sec. 4.3,
 // remark 2: preordering by level), its self-check and the publication
 // buffer.  Built once per direction; allocates and synchronises s.
@@ -596,7 +627,7 @@ sptrsv_status_t build_permuted(sptrsv_plan_t P, bool trans, cudaStream_t s) {
     if (e == cudaSuccess) e = launch_exclusive_scan(lens, pptr, n, s);
     if (e == cudaSuccess)
         e = launch_permute_rows(P->f64, n, ptr, idx, vmap, P->vals, L.jlev, L.ipos, pptr, pidx,
-                                pvals, P->num_sms * 16, s);
+                                pvals, P->num_sms * 16, s, copy_diag(P, trans));
     if (e == cudaSuccess) e = launch_verify_permuted(n, pptr, pidx, P->status, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     sptrsv_status_t rc = e == cudaSuccess ? SPTRSV_OK : cuda_fail(e);
@@ -651,7 +682,7 @@ cudaError_t refresh_permuted(sptrsv_plan_t P, cudaStream_t s) {
         cudaError_t e = launch_permute_rows(P->f64, P->n, d ? P->tptr : P->rowptr,
                                             d ? P->tidx : P->colidx, d ? P->tmap : nullptr,
                                             P->vals, L.jlev, L.ipos, L.pptr, nullptr, L.pvals,
-                                            P->num_sms * 16, s);
+                                            P->num_sms * 16, s, copy_diag(P, d));
         if (e != cudaSuccess) return e;
     }
     for (int d = 0; d < 2; ++d) {
@@ -660,8 +691,22 @@ cudaError_t refresh_permuted(sptrsv_plan_t P, cudaStream_t s) {
         cudaError_t e = launch_permute_rows(P->f64, P->n, d ? P->tptr : P->rowptr,
                                             d ? P->tidx : P->colidx, d ? P->tmap : nullptr,
                                             P->vals, L.qord, L.qipos, L.qptr, nullptr, L.qvals,
-                                            P->num_sms * 16, s);
+                                            P->num_sms * 16, s, copy_diag(P, d));
         if (e != cudaSuccess) return e;
+    }
+    // the FP32 copies of the refined solve, from the refreshed FP32 values
+    for (int d = 0; d < 2 && P->vals32; ++d) {
+        Levels& L = d ? P->trn : P->fwd;
+        for (int parts = 0; parts < 2; ++parts) {
+            void* v = parts ? L.qvals32 : L.pvals32;
+            if (!v) continue;
+            cudaError_t e = launch_permute_rows(
+                false, P->n, d ? P->tptr : P->rowptr, d ? P->tidx : P->colidx,
+                d ? P->tmap : nullptr, P->vals32, parts ? L.qord : L.jlev,
+                parts ? L.qipos : L.ipos, parts ? L.qptr : L.pptr, nullptr, v, P->num_sms * 16, s,
+                copy_diag(P, d));
+            if (e != cudaSuccess) return e;
+        }
     }
     return cudaSuccess;
 }
@@ -686,10 +731,13 @@ int resolve_part_rows(sptrsv_plan_t P) {
 }
 
 // Part-ordered copy of one direction's pattern and values for the
-// partitioned solve: the level order jlev stably re-sorted by part, its
-// inverse, the copy with columns renumbered to positions, its self-check
-// (every entry names its own or an earlier position) and the publication
-// buffer.  Allocates and synchronises s.
+// partitioned solve (layout in solve_parts.cu): the independent blocks of the
+// substitution order and their depths, the parts (balanced pieces of long
+// blocks, short blocks packed together) and their hand-out order (deepest
+// block first), the level order jlev stably re-sorted by part, its inverse,
+// the copy with columns renumbered to positions, its self-check (every entry
+// names its own or an earlier position) and the publication buffer.
+// Allocates and synchronises s.
 sptrsv_status_t build_parts(sptrsv_plan_t P, bool trans, cudaStream_t s) {
     Levels& L = trans ? P->trn : P->fwd;
     const int S = resolve_part_rows(P);
@@ -703,43 +751,110 @@ sptrsv_status_t build_parts(sptrsv_plan_t P, bool trans, cudaStream_t s) {
     const int* ptr = trans ? P->tptr : P->rowptr;
     const int* idx = trans ? P->tidx : P->colidx;
     const int* vmap = trans ? P->tmap : nullptr;
-    const int nparts = (int)(((long long)n + S - 1) / S);
     const size_t nz = nnz > 0 ? (size_t)nnz : 1;
+    const size_t N = (size_t)n;
     const int hist_n = radix_hist_entries(n);
     int *qord = nullptr, *qipos = nullptr, *qptr = nullptr, *qidx = nullptr, *scratch = nullptr;
+    int* qpart = nullptr;
     void *qvals = nullptr, *xq = nullptr;
-    cudaError_t e = cudaMalloc(&qord, sizeof(int) * (size_t)n);
-    if (e == cudaSuccess) e = cudaMalloc(&qipos, sizeof(int) * (size_t)n);
-    if (e == cudaSuccess) e = cudaMalloc(&qptr, sizeof(int) * ((size_t)n + 1));
+    cudaError_t e = cudaMalloc(&qord, sizeof(int) * N);
+    if (e == cudaSuccess) e = cudaMalloc(&qipos, sizeof(int) * N);
+    if (e == cudaSuccess) e = cudaMalloc(&qptr, sizeof(int) * (N + 1));
     if (e == cudaSuccess) e = cudaMalloc(&qidx, sizeof(int) * nz);
     if (e == cudaSuccess) e = cudaMalloc(&qvals, esize * nz);
-    if (e == cudaSuccess) e = cudaMalloc(&xq, esize * (size_t)n);
-    // scratch: key, lens | radix sort: 4 n + 2 hist
-    if (e == cudaSuccess)
-        e = cudaMalloc(&scratch, sizeof(int) * (6 * (size_t)n + 2 * (size_t)hist_n));
-    int* key = scratch;
-    int* lens = key + n;
-    int* k_a = lens + n;
-    int* v_a = k_a + n;
-    int* k_b = v_a + n;
-    int* v_b = k_b + n;
-    int* hist = v_b + n;
+    if (e == cudaSuccess) e = cudaMalloc(&xq, esize * N);
+    // scratch (ints): diff n+1, cover n+2, bflag n, bscan n+1, bstart n+1,
+    // depth n, pflag n, pscan n+1, pstart n+1, pkey n, horder n, prank n,
+    // psize n, rowkey n, lens n, 2 counters | radix sort: 4 n + 2 hist
+    const size_t scratch_ints = 22 * N + 16 + 2 * (size_t)hist_n;
+    if (e == cudaSuccess) e = cudaMalloc(&scratch, sizeof(int) * scratch_ints);
+    int* diff = scratch;
+    int* cover = diff + (N + 1);
+    int* bflag = cover + (N + 2);
+    int* bscan = bflag + N;
+    int* bstart = bscan + (N + 1);
+    int* depth = bstart + (N + 1);
+    int* pflag = depth + N;
+    int* pscan = pflag + N;
+    int* pstart = pscan + (N + 1);
+    int* pkey = pstart + (N + 1);
+    int* horder = pkey + N;
+    int* prank = horder + N;
+    int* psize = prank + N;
+    int* rowkey = psize + N;
+    int* lens = rowkey + N;
+    int* counters = lens + N;  // [0] longest part
+    int* k_a = counters + 8;
+    int* v_a = k_a + N;
+    int* k_b = v_a + N;
+    int* v_b = k_b + N;
+    int* hist = v_b + N;
     int* hist_scan = hist + hist_n;
-    if (e == cudaSuccess) e = launch_part_keys(n, L.jlev, S, upper, key, s);
+    int* piece = hist_scan + hist_n;
+    int* pkey2 = piece + N;
+    int* horder1 = pkey2 + N;
+    int nb = 0, np = 0, maxpart = 0;
+    // independent blocks: no dependency span covers their first position
+    if (e == cudaSuccess) e = cudaMemsetAsync(diff, 0, sizeof(int) * (N + 1), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(depth, 0, sizeof(int) * N, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, sizeof(int) * 8, s);
+    if (e == cudaSuccess) e = launch_part_spans(n, ptr, idx, upper, diff, s);
+    if (e == cudaSuccess) e = launch_exclusive_scan(diff, cover, n + 1, s);
+    if (e == cudaSuccess) e = launch_block_flags(n, cover, bflag, s);
+    if (e == cudaSuccess) e = launch_exclusive_scan(bflag, bscan, n, s);
+    if (e == cudaSuccess) e = launch_flag_scatter(n, bflag, bscan, bstart, s);
+    if (e == cudaSuccess) e = launch_block_depth(n, upper, L.lev, bscan, depth, s);
+    // parts, numbered in order of substitution
+    if (e == cudaSuccess) e = launch_part_flags(n, S, bscan, bstart, pflag, s);
+    if (e == cudaSuccess) e = launch_exclusive_scan(pflag, pscan, n, s);
+    if (e == cudaSuccess) e = launch_flag_scatter(n, pflag, pscan, pstart, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&nb, bscan + n, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&np, pscan + n, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && (np < 1 || np > n || nb < 1 || nb > n)) e = cudaErrorUnknown;
+    if (e == cudaSuccess) e = cudaMalloc(&qpart, sizeof(int) * ((size_t)np + 1));
+    // hand-out order: by piece index inside the block (every first piece,
+    // then every second piece, ...), deepest block first among equal pieces,
+    // then order of substitution (SPTRSV_PART_ORDER=1: deepest block first,
+    // its pieces together)
+    const int maxdepth = L.nlev > 0 ? L.nlev - 1 : 0;
+    const bool by_piece = env_ll("SPTRSV_PART_ORDER", 2) != 1;
     if (e == cudaSuccess)
-        e = radix_sort_values(key, L.jlev, n, bits_for(nparts - 1), qord, k_a, v_a, k_b, v_b,
+        e = launch_part_depth_keys(np, maxdepth, pstart, bscan, depth, pkey, s);
+    if (e == cudaSuccess)
+        e = radix_sort_values(pkey, nullptr, np, bits_for(maxdepth),
+                              by_piece ? horder1 : horder, k_a, v_a, k_b, v_b, hist, hist_scan,
+                              P->status, s);
+    if (by_piece) {
+        if (e == cudaSuccess) e = launch_part_piece(np, pstart, bscan, bstart, pscan, piece, s);
+        if (e == cudaSuccess) e = launch_gather(piece, np, horder1, np, pkey2, P->status, s);
+        if (e == cudaSuccess)
+            e = radix_sort_values(pkey2, horder1, np, bits_for(np - 1), horder, k_a, v_a, k_b,
+                                  v_b, hist, hist_scan, P->status, s);
+    }
+    if (e == cudaSuccess) e = launch_inverse_perm(horder, np, prank, s);
+    if (e == cudaSuccess) e = launch_part_sizes(np, horder, pstart, psize, counters, s);
+    if (e == cudaSuccess) e = launch_exclusive_scan(psize, qpart, np, s);
+    if (e == cudaSuccess) e = launch_row_part_keys(n, L.jlev, upper, pscan, prank, rowkey, s);
+    // the copy: rows by part (hand-out order), by level inside a part
+    if (e == cudaSuccess)
+        e = radix_sort_values(rowkey, L.jlev, n, bits_for(np - 1), qord, k_a, v_a, k_b, v_b,
                               hist, hist_scan, P->status, s);
     if (e == cudaSuccess) e = launch_inverse_perm(qord, n, qipos, s);
     if (e == cudaSuccess) e = launch_ordered_lengths(n, ptr, qord, lens, s);
     if (e == cudaSuccess) e = launch_exclusive_scan(lens, qptr, n, s);
     if (e == cudaSuccess)
         e = launch_permute_rows(P->f64, n, ptr, idx, vmap, P->vals, qord, qipos, qptr, qidx,
-                                qvals, P->num_sms * 16, s);
+                                qvals, P->num_sms * 16, s, copy_diag(P, trans));
     if (e == cudaSuccess) e = launch_verify_permuted(n, qptr, qidx, P->status, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&maxpart, counters, sizeof(int),
+                                              cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    sptrsv_status_t rc = e == cudaSuccess ? SPTRSV_OK : cuda_fail(e);
+    sptrsv_status_t rc = e == cudaSuccess ? SPTRSV_OK
+                         : e == cudaErrorUnknown ? SPTRSV_ERR_INTERNAL : cuda_fail(e);
     int row = -1;
     if (rc == SPTRSV_OK && take_status(P, s, &row) != SPTRSV_OK) rc = SPTRSV_ERR_INTERNAL;
+    if (rc == SPTRSV_OK && (maxpart < 1 || maxpart > S)) rc = SPTRSV_ERR_INTERNAL;
     cudaFree(scratch);
     if (rc != SPTRSV_OK) {
         cudaFree(qord);
@@ -748,6 +863,7 @@ sptrsv_status_t build_parts(sptrsv_plan_t P, bool trans, cudaStream_t s) {
         cudaFree(qidx);
         cudaFree(qvals);
         cudaFree(xq);
+        cudaFree(qpart);
         return rc;
     }
     L.qS = S;
@@ -757,6 +873,40 @@ sptrsv_status_t build_parts(sptrsv_plan_t P, bool trans, cudaStream_t s) {
     L.qidx = qidx;
     L.qvals = qvals;
     L.xq = xq;
+    L.qpart = qpart;
+    L.qnparts = np;
+    L.qmaxpart = maxpart;
+    L.qnblocks = nb;
+    return SPTRSV_OK;
+}
+
+// FP32 values (gathered from the plan's FP32 copy vals32) and an FP32
+// publication buffer for the level-ordered (parts = false) or part-ordered
+// (parts = true) copy of an F64 plan, whose pattern must exist.  Allocates.
+sptrsv_status_t build_copy_f32(sptrsv_plan_t P, bool trans, bool parts, cudaStream_t s) {
+    Levels& L = trans ? P->trn : P->fwd;
+    void*& vals = parts ? L.qvals32 : L.pvals32;
+    void*& xpub = parts ? L.xq32 : L.xp32;
+    if (vals) return SPTRSV_OK;
+    if (!P->vals32 && P->nnz > 0) return SPTRSV_ERR_NOT_SUPPORTED;
+    if (capturing(s)) return SPTRSV_ERR_NOT_SUPPORTED;
+    const size_t nz = P->nnz > 0 ? (size_t)P->nnz : 1;
+    void *v = nullptr, *xq = nullptr;
+    cudaError_t e = cudaMalloc(&v, sizeof(float) * nz);
+    if (e == cudaSuccess) e = cudaMalloc(&xq, sizeof(float) * (size_t)P->n);
+    if (e == cudaSuccess)
+        e = launch_permute_rows(false, P->n, trans ? P->tptr : P->rowptr,
+                                trans ? P->tidx : P->colidx, trans ? P->tmap : nullptr, P->vals32,
+                                parts ? L.qord : L.jlev, parts ? L.qipos : L.ipos,
+                                parts ? L.qptr : L.pptr, nullptr, v, P->num_sms * 16, s,
+                                copy_diag(P, trans));
+    if (e != cudaSuccess) {
+        cudaFree(v);
+        cudaFree(xq);
+        return cuda_fail(e);
+    }
+    vals = v;
+    xpub = xq;
     return SPTRSV_OK;
 }
 
@@ -794,9 +944,18 @@ sptrsv_status_t prof_end(sptrsv_plan_t P, cudaStream_t s) {
 
 // One triangular solve (forward pattern or transpose) of any element type:
 // `f64` selects the kernels, `vals` the values they read.
+// Whether a solve of this form can accumulate its published values into an
+// FP64 array (SolveParams::xacc).
+bool accumulates(sptrsv_algo_t algo, int nrhs) {
+    if (algo == SPTRSV_ALGO_LEVEL) return false;
+    return nrhs > 1 || algo == SPTRSV_ALGO_SELF || algo == SPTRSV_ALGO_SELF_PERMUTED ||
+           algo == SPTRSV_ALGO_SELF_BLOCKED || algo == SPTRSV_ALGO_SELF_PARTITIONED;
+}
+
 sptrsv_status_t run_solve(sptrsv_plan_t P, bool trans, bool f64, const void* vals, const void* b,
                           long long ldb, void* x, long long ldx, int nrhs, sptrsv_algo_t algo,
-                          cudaStream_t s) {
+                          cudaStream_t s, double* xacc = nullptr, long long ldacc = 0,
+                          bool acc_first = false) {
     const bool mrhs = nrhs > 1;
     // multi-RHS solves have a launch shape of their own (sptrsv_set_mrhs_tuning);
     // a single-RHS solve takes its algorithm's shape if one was set
@@ -809,15 +968,32 @@ sptrsv_status_t run_solve(sptrsv_plan_t P, bool trans, bool f64, const void* val
     const int max_blocks = mrhs ? (P->mrhs_max_blocks >= 0 ? P->mrhs_max_blocks : P->max_blocks)
                                 : (own ? P->alg_max_blocks[a] : P->max_blocks);
     if (algo == SPTRSV_ALGO_SELF_CHAINS && !mrhs) ST(build_chain(P, trans, lanes, s));
-    // the level-ordered copy holds the plan's own element type
-    const bool blocked = algo == SPTRSV_ALGO_SELF_BLOCKED && !mrhs && f64 == P->f64;
-    const bool permuted =
-        (algo == SPTRSV_ALGO_SELF_PERMUTED || blocked) && !mrhs && f64 == P->f64;
+    // The copies hold the plan's element type, and FP32 values beside them
+    // for the FP32 solves of a refined F64 plan (f64 != P->f64).
+    const bool f32_of_f64 = !f64 && P->f64;
+    if (f64 != P->f64 && !f32_of_f64) return SPTRSV_ERR_INVALID_ARG;
+    const bool blocked = algo == SPTRSV_ALGO_SELF_BLOCKED && !mrhs;
+    const bool permuted = (algo == SPTRSV_ALGO_SELF_PERMUTED || blocked) && !mrhs;
     if (permuted) ST(build_permuted(P, trans, s));
+    if (permuted && f32_of_f64) ST(build_copy_f32(P, trans, false, s));
     const bool column = algo == SPTRSV_ALGO_SELF_COLUMN && !mrhs;
     if (column) ST(build_column(P, trans, s));
-    const bool parts = algo == SPTRSV_ALGO_SELF_PARTITIONED && !mrhs && f64 == P->f64;
+    const bool parts = algo == SPTRSV_ALGO_SELF_PARTITIONED && !mrhs;
     if (parts) ST(build_parts(P, trans, s));
+    if (parts && f32_of_f64) ST(build_copy_f32(P, trans, true, s));
+    // multi-RHS solves of the copying forms run on the level-ordered copy
+    // (the shared-memory tiles of the blocked and partitioned forms hold one
+    // column): the multi-RHS kernel with a position-ordered publication buffer
+    const bool mrhs_copy = mrhs && (algo == SPTRSV_ALGO_SELF_PERMUTED ||
+                                    algo == SPTRSV_ALGO_SELF_BLOCKED ||
+                                    algo == SPTRSV_ALGO_SELF_PARTITIONED);
+    if (mrhs_copy) {
+        Levels& Lw = trans ? P->trn : P->fwd;
+        ST(build_permuted(P, trans, s));
+        if (f32_of_f64) ST(build_copy_f32(P, trans, false, s));
+        ST(ensure_bytes(&Lw.xpm, &Lw.xpm_bytes,
+                        (f64 ? sizeof(double) : sizeof(float)) * (size_t)P->n * nrhs, s));
+    }
     const Levels& L = trans ? P->trn : P->fwd;
     SolveParams p;
     memset(&p, 0, sizeof(p));
@@ -839,6 +1015,10 @@ sptrsv_status_t run_solve(sptrsv_plan_t P, bool trans, bool f64, const void* val
     p.spin = P->spin;
     p.withhold = P->withhold;
     p.ipos = (algo == SPTRSV_ALGO_SELF_TILED && P->tile_level_order) ? L.ipos : nullptr;
+    if (xacc && !accumulates(algo, nrhs)) return SPTRSV_ERR_INVALID_ARG;
+    p.xacc = xacc;
+    p.ldacc = ldacc;
+    p.acc_first = acc_first ? 1 : 0;
     int launches = 0;
     if (algo == SPTRSV_ALGO_LEVEL) {
         ST(prof_begin(P, s));
@@ -881,22 +1061,47 @@ sptrsv_status_t run_solve(sptrsv_plan_t P, bool trans, bool f64, const void* val
         p.ptr = L.qptr;
         p.idx = L.qidx;
         p.vmap = nullptr;
-        p.vals = L.qvals;
-        p.xp = L.xq;
+        p.vals = f32_of_f64 ? L.qvals32 : L.qvals;
+        p.xp = f32_of_f64 ? L.xq32 : L.xq;
+        p.prescaled = P->unit ? 0 : 1;
         p.jlev = L.qord;
-        CK(launch_prep_self(f64, P->n, 1, L.xq, 1, nullptr, 0, nullptr, P->counters,
+        p.part_ptr = L.qpart;
+        p.nparts = L.qnparts;
+        CK(launch_prep_self(f64, P->n, 1, p.xp, 1, nullptr, 0, nullptr, P->counters,
                             P->num_sms * 8, s));
         const int cl = P->part_cluster;
-        const long long tiles = ((long long)P->n + L.qS - 1) / L.qS;
-        const long long groups = (tiles + cl - 1) / cl;
-        long long grid = blocked_resident_blocks(f64, lanes, cl, block, L.qS, P->num_sms);
+        const long long groups = ((long long)L.qnparts + cl - 1) / cl;
+        long long grid = blocked_resident_blocks(f64, lanes, cl, block, L.qmaxpart, P->num_sms);
         if (grid < cl) return SPTRSV_ERR_INVALID_ARG;  // this shape cannot run
         if (max_blocks > 0 && grid > max_blocks) grid = max_blocks;
         if (grid > groups * cl) grid = groups * cl;
         grid = grid / cl * cl;
         if (grid < cl) grid = cl;
         ST(prof_begin(P, s));
-        CK(launch_blocked_k1(f64, lanes, p, L.qS, (int)grid, block, s, cl));
+        CK(launch_blocked_k1(f64, lanes, p, L.qmaxpart, (int)grid, block, s, cl));
+        ST(prof_end(P, s));
+        launches = 2;
+    } else if (mrhs_copy) {
+        // Columns publish to the position-ordered buffer L.xpm ([n][nrhs]) and
+        // store x(i) for the caller; every b(i, c) is read by row i before
+        // x(i, c) is written, so an in-place solve needs no copy of b.
+        p.ptr = L.pptr;
+        p.idx = L.pidx;
+        p.vmap = nullptr;
+        p.vals = f32_of_f64 ? L.pvals32 : L.pvals;
+        p.xp = L.xpm;
+        p.prescaled = P->unit ? 0 : 1;
+        CK(launch_prep_self(f64, P->n, nrhs, L.xpm, nrhs, nullptr, 0, nullptr, P->counters,
+                            P->num_sms * 8, s));
+        const int R = 32 / lanes;
+        const long long tickets = ((long long)P->n + R - 1) / R;
+        const long long want_blocks = (tickets + block / 32 - 1) / (block / 32);
+        long long grid = (long long)self_blocks_per_sm(f64, lanes, true, false, block) * P->num_sms;
+        if (max_blocks > 0 && grid > max_blocks) grid = max_blocks;
+        if (grid > want_blocks) grid = want_blocks;
+        if (grid < 1) grid = 1;
+        ST(prof_begin(P, s));
+        CK(launch_mrhs(f64, lanes, true, p, (int)grid, block, s));
         ST(prof_end(P, s));
         launches = 2;
     } else if (permuted) {
@@ -906,9 +1111,10 @@ sptrsv_status_t run_solve(sptrsv_plan_t P, bool trans, bool f64, const void* val
         p.ptr = L.pptr;
         p.idx = L.pidx;
         p.vmap = nullptr;
-        p.vals = L.pvals;
-        p.xp = L.xp;
-        CK(launch_prep_self(f64, P->n, 1, L.xp, 1, nullptr, 0, nullptr, P->counters,
+        p.vals = f32_of_f64 ? L.pvals32 : L.pvals;
+        p.xp = f32_of_f64 ? L.xp32 : L.xp;
+        p.prescaled = P->unit ? 0 : 1;
+        CK(launch_prep_self(f64, P->n, 1, p.xp, 1, nullptr, 0, nullptr, P->counters,
                             P->num_sms * 8, s));
         const int R = 32 / lanes;
         const long long tickets = ((long long)P->n + R - 1) / R;
@@ -990,8 +1196,9 @@ sptrsv_status_t solve_common(sptrsv_plan_t P, bool trans, const void* b, void* x
         (algo != SPTRSV_ALGO_LEVEL && algo != SPTRSV_ALGO_SELF && algo != SPTRSV_ALGO_SELF_TILED &&
          algo != SPTRSV_ALGO_SELF_CHAINS && algo != SPTRSV_ALGO_SELF_PERMUTED &&
          algo != SPTRSV_ALGO_SELF_COLUMN && algo != SPTRSV_ALGO_SELF_BLOCKED &&
-         algo != SPTRSV_ALGO_SELF_PARTITIONED))
+         algo != SPTRSV_ALGO_SELF_PARTITIONED && algo != SPTRSV_ALGO_AUTO))
         return SPTRSV_ERR_INVALID_ARG;
+    if (algo == SPTRSV_ALGO_AUTO) algo = P->default_algo;
     P->last_launches = 0;
     if (P->n == 0) return SPTRSV_OK;
     if (!b || !x) return SPTRSV_ERR_INVALID_ARG;
@@ -1162,6 +1369,33 @@ sptrsv_status_t sptrsv_prepare_transpose(sptrsv_plan_t plan, void* stream) {
     return build_transpose(plan, (cudaStream_t)stream);
 }
 
+sptrsv_status_t sptrsv_prepare(sptrsv_plan_t plan, int transpose, sptrsv_algo_t algo,
+                               void* stream) {
+    if (!plan || (transpose != 0 && transpose != 1) || (int)algo < SPTRSV_ALGO_LEVEL ||
+        (int)algo > SPTRSV_ALGO_AUTO)
+        return SPTRSV_ERR_INVALID_ARG;
+    sptrsv_plan_t P = plan;
+    if (P->n == 0) return SPTRSV_OK;
+    DeviceGuard g(P->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (capturing(s)) return SPTRSV_ERR_NOT_SUPPORTED;
+    if (algo == SPTRSV_ALGO_AUTO) algo = P->default_algo;
+    const bool trans = transpose != 0;
+    if (trans) ST(build_transpose(P, s));
+    const int a = (int)algo;
+    const int lanes = P->alg_lanes[a] > 0 ? P->alg_lanes[a] : P->lanes;
+    switch (algo) {
+        case SPTRSV_ALGO_SELF_CHAINS: ST(build_chain(P, trans, lanes, s)); break;
+        case SPTRSV_ALGO_SELF_PERMUTED:
+        case SPTRSV_ALGO_SELF_BLOCKED: ST(build_permuted(P, trans, s)); break;
+        case SPTRSV_ALGO_SELF_PARTITIONED: ST(build_parts(P, trans, s)); break;
+        case SPTRSV_ALGO_SELF_COLUMN: ST(build_column(P, trans, s)); break;
+        default: break;
+    }
+    CK(cudaStreamSynchronize(s));
+    return SPTRSV_OK;
+}
+
 sptrsv_status_t sptrsv_grad_vals(sptrsv_plan_t plan, const void* d_y, const void* d_x, int nrhs,
                                  int ld, void* d_gvals, void* stream) {
     if (!plan || nrhs < 1 || ld < nrhs) return SPTRSV_ERR_INVALID_ARG;
@@ -1239,20 +1473,39 @@ sptrsv_status_t sptrsv_solve_refined(sptrsv_plan_t plan, const double* d_b, doub
     }
     if (!P->stats) CK(cudaMalloc(&P->stats, 4 * sizeof(unsigned long long)));
     CK(cudaMemsetAsync(P->stats, 0, 4 * sizeof(unsigned long long), s));
+    // The FP32 solves run the plan's default form (sptrsv_set_default_algo,
+    // e.g. the autotuner's choice) with that form's launch shape.  The forms
+    // that can accumulate add each published correction straight into the
+    // FP64 solution x (no separate update pass); the others store it in an
+    // FP32 vector that an update pass adds.
+    const sptrsv_algo_t algo = P->default_algo;
+    const bool fused = accumulates(algo, nrhs);
     int launches = 0;
+    auto correction = [&](bool first) -> sptrsv_status_t {
+        if (fused) {
+            ST(run_solve(P, false, false, P->vals32, P->r32, nrhs, P->d32, nrhs, nrhs, algo, s,
+                         d_x, ld, first));
+            launches += P->last_launches;
+        } else {
+            ST(run_solve(P, false, false, P->vals32, P->r32, nrhs, P->d32, nrhs, nrhs, algo, s));
+            launches += P->last_launches;
+            CK(launch_update(n, nrhs, d_x, ld, P->d32, first, nullptr, grid, s));
+            launches += 1;
+        }
+        return SPTRSV_OK;
+    };
     // x0 = 0, so r0 = b: the first FP32 solve is of b itself.
     CK(launch_to_f32(n, nrhs, d_b, ld, P->r32, P->stats + 3, grid, s));
-    ST(run_solve(P, false, false, P->vals32, P->r32, nrhs, P->d32, nrhs, nrhs, SPTRSV_ALGO_SELF, s));
-    launches += 1 + P->last_launches;
-    CK(launch_update(n, nrhs, d_x, ld, P->d32, true, P->stats + 2, grid, s));
     launches += 1;
+    ST(correction(true));
     int it = 0;
     double rel = 0.0;
     for (;;) {
-        CK(cudaMemsetAsync(P->stats, 0, sizeof(unsigned long long), s));
+        // r = b - A x in FP64, its FP32 copy (the next right-hand side),
+        // max|r|, max|x| and (first pass) ||A||_inf, in one pass
+        CK(cudaMemsetAsync(P->stats, 0, 3 * sizeof(unsigned long long), s));
         CK(launch_residual(P->lanes, n, P->rowptr, P->colidx, (const double*)P->vals, P->unit,
-                           nrhs, d_b, ld, d_x, ld, nullptr, 0, P->r32, P->stats, it == 0, grid,
-                           s));
+                           nrhs, d_b, ld, d_x, ld, nullptr, 0, P->r32, P->stats, true, grid, s));
         launches += 1;
         unsigned long long h[4];
         CK(cudaMemcpyAsync(h, P->stats, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -1262,17 +1515,26 @@ sptrsv_status_t sptrsv_solve_refined(sptrsv_plan_t plan, const double* d_b, doub
         const double denom = st[3] + st[1] * st[2];
         rel = denom > 0.0 ? st[0] / denom : (st[0] > 0.0 ? INFINITY : 0.0);
         if (rel <= tol || it >= max_iter) break;
-        ST(run_solve(P, false, false, P->vals32, P->r32, nrhs, P->d32, nrhs, nrhs,
-                     SPTRSV_ALGO_SELF, s));
-        launches += P->last_launches;
-        CK(cudaMemsetAsync(P->stats + 2, 0, sizeof(unsigned long long), s));
-        CK(launch_update(n, nrhs, d_x, ld, P->d32, false, P->stats + 2, grid, s));
-        launches += 1;
+        ST(correction(false));
         ++it;
     }
     if (iters) *iters = it;
     if (rel_resid) *rel_resid = rel;
     P->last_launches = launches;
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t sptrsv_set_default_algo(sptrsv_plan_t plan, sptrsv_algo_t algo) {
+    const int a = (int)algo;
+    if (!plan || a < SPTRSV_ALGO_LEVEL || a > SPTRSV_ALGO_SELF_PARTITIONED)
+        return SPTRSV_ERR_INVALID_ARG;
+    plan->default_algo = algo;
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t sptrsv_get_default_algo(sptrsv_plan_t plan, int* algo) {
+    if (!plan || !algo) return SPTRSV_ERR_INVALID_ARG;
+    *algo = (int)plan->default_algo;
     return SPTRSV_OK;
 }
 
@@ -1355,6 +1617,20 @@ sptrsv_status_t sptrsv_get_partition(sptrsv_plan_t plan, int* part_rows, int* cl
     if (!plan || !part_rows || !cluster_blocks) return SPTRSV_ERR_INVALID_ARG;
     *part_rows = resolve_part_rows(plan);
     *cluster_blocks = plan->part_cluster;
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t sptrsv_partition_info(sptrsv_plan_t plan, int transpose, int* nparts,
+                                      int* nblocks, int* max_part_rows, const int** d_part_ptr,
+                                      const int** d_order) {
+    if (!plan || (transpose != 0 && transpose != 1)) return SPTRSV_ERR_INVALID_ARG;
+    const Levels& L = transpose ? plan->trn : plan->fwd;
+    if (!L.qord && plan->n > 0) return SPTRSV_ERR_NOT_SUPPORTED;
+    if (nparts) *nparts = L.qnparts;
+    if (nblocks) *nblocks = L.qnblocks;
+    if (max_part_rows) *max_part_rows = L.qmaxpart;
+    if (d_part_ptr) *d_part_ptr = L.qpart;
+    if (d_order) *d_order = L.qord;
     return SPTRSV_OK;
 }
 

@@ -97,7 +97,7 @@ __global__ void residual_k(int n, const int* __restrict__ ptr, const int* __rest
     const int lane = threadIdx.x & 31;
     const int sl = lane % W;
     const unsigned gmask = group_mask<W>(lane);
-    double rmax = 0.0, amax = 0.0;
+    double rmax = 0.0, amax = 0.0, xmax = 0.0;
     // Every lane of a block runs the same number of iterations so that the
     // block-wide reduction below is reached by all of them.
     const long long first = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / W;
@@ -121,6 +121,7 @@ __global__ void residual_k(int n, const int* __restrict__ ptr, const int* __rest
                     if (r) r[i * ldr + c] = rr;
                     if (r32) r32[i * k + c] = (float)rr;
                     rmax = fmax(rmax, fabs(rr));
+                    xmax = fmax(xmax, fabs(x[i * ldx + c]));
                     if (c == 0) amax = fmax(amax, a_abs);
                 }
             }
@@ -128,6 +129,8 @@ __global__ void residual_k(int n, const int* __restrict__ ptr, const int* __rest
     }
     if (stats) {
         block_max_to(stats, rmax);
+        __syncthreads();
+        block_max_to(stats + 2, xmax);
         if (want_norm) {
             __syncthreads();
             block_max_to(stats + 1, amax);

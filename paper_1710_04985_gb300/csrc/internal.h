@@ -33,7 +33,27 @@ struct SolveParams {
     int kbeg, cnt;        // level-scheduled: this launch's slice of jlev
     void* xp;             // level-ordered solve: publication buffer in position
                           // order (nullptr: rows publish to x itself)
+    const int* part_ptr;  // blocked solve: first position of each tile (nparts + 1
+                          // entries; nullptr: tiles of tile_rows positions)
+    int nparts;
+    // FP64 accumulation of the published values (the FP32 solves of the
+    // refined solve): xacc[i][c] = v (acc_first) or xacc[i][c] += v.
+    // nullptr: off.  The copying forms then skip their store to x.
+    double* xacc;
+    long long ldacc;
+    int acc_first;
+    // the values are a pre-scaled copy (1/d(i) in the diagonal's slot, a_ij /
+    // d(i) elsewhere; non-unit matrices): no division or scaling in the solve
+    int prescaled;
 };
+
+// Adds (or stores) the published value v of row i, column c into p.xacc.
+template <typename T>
+__device__ __forceinline__ void accumulate_published(const SolveParams& p, long long i, int c,
+                                                     T v) {
+    double* a = p.xacc + i * p.ldacc + c;
+    *a = p.acc_first ? (double)v : *a + (double)v;
+}
 
 // Column structure of the column-wise solve (solve_column.cu): the CSR of
 // the transpose of the system matrix, so row i lists the unknowns that
@@ -83,7 +103,7 @@ int column_blocks_per_sm(bool f64, int lanes, bool cmap, int block);
 // Blocked self-scheduled solve on the level- or part-ordered copy
 // (solve_blocked.cu): a block per tile of tile_rows consecutive positions,
 // in-tile dependencies through shared memory (tile_rows * element size at
-// most the device's opt-in shared memory per block, minus 64 B).
+// most the device's opt-in shared memory per block, minus 128 B).
 // cluster in {1, 2, 4, 8}: clusters of that many blocks take consecutive
 // tiles together and read each other's tiles in distributed shared memory;
 // grid must then be a multiple of cluster.
@@ -95,22 +115,50 @@ int blocked_resident_blocks(bool f64, int lanes, int cluster, int block, int til
 // Resident blocks per SM of the level-ordered-copy form of self_solve_k1.
 int self_perm_blocks_per_sm(bool f64, int lanes, int block);
 
-// ---- partitioned solve (solve_parts.cu): key[k] = part of row jlev[k], parts
-// of S consecutive rows in order of substitution (ascending rows for a lower
-// system, descending for an upper one).
-cudaError_t launch_part_keys(int n, const int* jlev, int S, bool upper, int* key,
-                             cudaStream_t s);
+// ---- partitioned solve (solve_parts.cu).  Positions t are in order of
+// substitution (row t of a lower system, row n-1-t of an upper one).
+// diff[0..n] (zeroed by the caller) gets +1 at f+1 and -1 at t+1 for every
+// row at t whose farthest dependency is at f < t.
+cudaError_t launch_part_spans(int n, const int* ptr, const int* idx, bool upper, int* diff,
+                              cudaStream_t s);
+// flag[t] = 1 where cover[t+1] (the exclusive scan of diff) is 0, or t = 0.
+cudaError_t launch_block_flags(int n, const int* cover, int* flag, cudaStream_t s);
+// start[scan[t]] = t where flag[t] (scan = exclusive scan of flag, n + 1
+// entries); start[scan[n]] = n.
+cudaError_t launch_flag_scatter(int n, const int* flag, const int* scan, int* start,
+                                cudaStream_t s);
+// depth[b] = max level of block b's rows (depth zeroed by the caller).
+cudaError_t launch_block_depth(int n, bool upper, const int* lev, const int* bscan, int* depth,
+                               cudaStream_t s);
+// Part starts: balanced pieces of at most S rows of every block longer than
+// S / 2, consecutive shorter blocks packed by windows of S / 2 positions.
+cudaError_t launch_part_flags(int n, int S, const int* bscan, const int* bstart, int* flag,
+                              cudaStream_t s);
+cudaError_t launch_part_depth_keys(int np, int maxdepth, const int* pstart, const int* bscan,
+                                   const int* depth, int* key, cudaStream_t s);
+// piece[p] = index of part p among the parts of its block.
+cudaError_t launch_part_piece(int np, const int* pstart, const int* bscan, const int* bstart,
+                              const int* pscan, int* piece, cudaStream_t s);
+// size[r] = rows of part horder[r]; *maxsize = max (zeroed by the caller).
+cudaError_t launch_part_sizes(int np, const int* horder, const int* pstart, int* size,
+                              int* maxsize, cudaStream_t s);
+// key[k] = prank[part of row jlev[k]].
+cudaError_t launch_row_part_keys(int n, const int* jlev, bool upper, const int* pscan,
+                                 const int* prank, int* key, cudaStream_t s);
 
 // ---- level-ordered copy (permute.cu)
 // lens[k] = length of row jlev[k].
 cudaError_t launch_ordered_lengths(int n, const int* ptr, const int* jlev, int* lens,
                                    cudaStream_t s);
 // Row k of the copy = row jlev[k] in entry order: pidx = ipos[idx] (skipped
-// when pidx is nullptr, a values-only refresh), pvals = vals[vmap[q] or q].
+// when pidx is nullptr, a values-only refresh), pvals = vals[vmap[q] or q];
+// diag >= 0: pre-scaled by 1/d(i), with 1/d(i) in the diagonal's slot (the
+// diagonal is the first entry of a row for diag = 1, the last for 0); -1:
+// copied as they are (unit diagonal).
 cudaError_t launch_permute_rows(bool f64, int n, const int* ptr, const int* idx, const int* vmap,
                                 const void* vals, const int* jlev, const int* ipos,
                                 const int* pptr, int* pidx, void* pvals, int grid,
-                                cudaStream_t s);
+                                cudaStream_t s, int diag);
 // Self-check: every entry of row k names k or an earlier position.
 cudaError_t launch_verify_permuted(int n, const int* pptr, const int* pidx,
                                    unsigned long long* status, cudaStream_t s);
@@ -188,8 +236,9 @@ cudaError_t launch_grad_vals(bool f64, int lanes, int n, const int* ptr, const i
                              const void* y, long long ldy, const void* x, long long ldx, int k,
                              void* g, cudaStream_t s, int grid);
 // r = b - A x in FP64; writes r (nullable, [n][ldr]) and r32 (nullable,
-// contiguous [n][k]); stats (nullable): atomicMax of max|r| into stats[0]
-// and, if want_norm, of max_i sum_j |A_ij| into stats[1].
+// contiguous [n][k]); stats (nullable): atomicMax of max|r| into stats[0],
+// of max|x| into stats[2] and, if want_norm, of max_i sum_j |A_ij| into
+// stats[1].
 cudaError_t launch_residual(int lanes, int n, const int* ptr, const int* idx, const double* vals,
                             bool unit, int k, const double* b, long long ldb, const double* x,
                             long long ldx, double* r, long long ldr, float* r32,

@@ -16,6 +16,8 @@
 // header and the flags of its own rows before anything reads them.  Two calls
 // whose work overlaps on the GPU (different streams, or the same array reached
 // from two host threads) race on that array and give wrong results.
+#include <atomic>
+#include <cstdlib>
 #include <mutex>
 
 #include "internal.h"
@@ -68,7 +70,7 @@ template <typename T, int W>
 __global__ void __launch_bounds__(1024)
     noalloc_solve_k(int n, const int* __restrict__ ptr, const int* __restrict__ idx,
                     const T* __restrict__ vals, int upper, int unit, const T* b, T* x,
-                    unsigned char* scratch, SpinPolicy sp) {
+                    unsigned char* scratch, SpinPolicy sp, int withhold) {
     constexpr int R = 32 / W;
     constexpr int E = kChunk;
     constexpr unsigned FULL = 0xffffffffu;
@@ -156,7 +158,7 @@ __global__ void __launch_bounds__(1024)
             const T tot = group_sum<W>(sum, FULL);
             if (row_ready && !published) {
                 pubv = (bi - tot) * dinv;  // lane 0 of the group holds bi and dinv
-                if (sl == 0) {
+                if (sl == 0 && i != withhold) {  // test hook: no global publication
                     st_relaxed(x + i, pubv);
                     st_release(flags + i, 1);
                 }
@@ -204,48 +206,76 @@ __global__ void __launch_bounds__(1024)
     }
 }
 
+constexpr int kMaxDevices = 64;
+
+// Resident blocks per SM of noalloc_solve_k<T, W> at 256 threads, looked up
+// once per device (0: not yet known).
+template <typename T, int W>
+cudaError_t blocks_per_sm(int dev, int* out) {
+    static std::atomic<int> cache[kMaxDevices];
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v == 0) {
+        cudaError_t e =
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, noalloc_solve_k<T, W>, 256, 0);
+        if (e != cudaSuccess) return e;
+        if (v < 1) v = 1;
+        cache[dev].store(v, std::memory_order_relaxed);
+    }
+    *out = v;
+    return cudaSuccess;
+}
+
 template <typename T, int W>
 cudaError_t launch_w(int n, const int* ptr, const int* idx, const void* vals, bool upper,
-                     bool unit, const void* b, void* x, unsigned char* scratch, int num_sms,
-                     cudaStream_t s) {
+                     bool unit, const void* b, void* x, unsigned char* scratch, int dev,
+                     int num_sms, const SpinPolicy& sp, int withhold, cudaStream_t s) {
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, noalloc_solve_k<T, W>,
-                                                                  256, 0);
+    cudaError_t e = blocks_per_sm<T, W>(dev, &per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm > 4) per_sm = 4;
-    if (per_sm < 1) per_sm = 1;
     const long long tickets = ((long long)n + 32 / W - 1) / (32 / W);
     long long grid = (long long)per_sm * num_sms;
     if (grid > (tickets + 7) / 8) grid = (tickets + 7) / 8;
     if (grid < 1) grid = 1;
-    SpinPolicy sp{1ll << 24, 256, 128};
     noalloc_solve_k<T, W><<<(int)grid, 256, 0, s>>>(n, ptr, idx, (const T*)vals, upper, unit,
-                                                   (const T*)b, (T*)x, scratch, sp);
+                                                   (const T*)b, (T*)x, scratch, sp, withhold);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_t(int lanes, int n, const int* ptr, const int* idx, const void* vals,
                      bool upper, bool unit, const void* b, void* x, unsigned char* scratch,
-                     int num_sms, cudaStream_t s) {
+                     int dev, int num_sms, const SpinPolicy& sp, int withhold, cudaStream_t s) {
+#define SPTRSV_NOALLOC(WW)                                                                  \
+    return launch_w<T, WW>(n, ptr, idx, vals, upper, unit, b, x, scratch, dev, num_sms, sp, \
+                           withhold, s)
     switch (lanes) {
-        case 1: return launch_w<T, 1>(n, ptr, idx, vals, upper, unit, b, x, scratch, num_sms, s);
-        case 2: return launch_w<T, 2>(n, ptr, idx, vals, upper, unit, b, x, scratch, num_sms, s);
-        case 4: return launch_w<T, 4>(n, ptr, idx, vals, upper, unit, b, x, scratch, num_sms, s);
-        case 8: return launch_w<T, 8>(n, ptr, idx, vals, upper, unit, b, x, scratch, num_sms, s);
-        case 16: return launch_w<T, 16>(n, ptr, idx, vals, upper, unit, b, x, scratch, num_sms, s);
-        default: return launch_w<T, 32>(n, ptr, idx, vals, upper, unit, b, x, scratch, num_sms, s);
+        case 1: SPTRSV_NOALLOC(1);
+        case 2: SPTRSV_NOALLOC(2);
+        case 4: SPTRSV_NOALLOC(4);
+        case 8: SPTRSV_NOALLOC(8);
+        case 16: SPTRSV_NOALLOC(16);
+        default: SPTRSV_NOALLOC(32);
     }
+#undef SPTRSV_NOALLOC
+}
+
+// A positive integer from the environment, else dflt.
+long long env_value(const char* name, long long dflt) {
+    const char* v = getenv(name);
+    if (!v || !*v) return dflt;
+    char* end = nullptr;
+    const long long x = strtoll(v, &end, 0);
+    return (end && *end == 0 && x > 0) ? x : dflt;
 }
 
 // Device address of the scratch array, looked up once per device with that
 // device current (the host-side symbol is only a stand-in, not an address).
-constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 unsigned char* g_scratch_addr[kMaxDevices] = {};
 int g_num_sms[kMaxDevices] = {};
 
-cudaError_t scratch_for_current_device(unsigned char** out, int* num_sms) {
+cudaError_t scratch_for_current_device(unsigned char** out, int* num_sms, int* device) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -263,6 +293,7 @@ cudaError_t scratch_for_current_device(unsigned char** out, int* num_sms) {
     }
     *out = g_scratch_addr[dev];
     *num_sms = g_num_sms[dev];
+    *device = dev;
     return cudaSuccess;
 }
 
@@ -290,8 +321,16 @@ extern "C" SPTRSV_API sptrsv_status_t sptrsv_solve_noalloc(
     }
     cudaStream_t s = (cudaStream_t)stream;
     unsigned char* scratch = nullptr;
-    int num_sms = 1;
-    if (scratch_for_current_device(&scratch, &num_sms) != cudaSuccess) return SPTRSV_ERR_CUDA;
+    int num_sms = 1, dev = 0;
+    if (scratch_for_current_device(&scratch, &num_sms, &dev) != cudaSuccess)
+        return SPTRSV_ERR_CUDA;
+    // the bounded wait: SPTRSV_SPIN_LIMIT polls (2^24 by default), read at
+    // every call; SPTRSV_DEBUG_NOALLOC_WITHHOLD = r (test hook) keeps row r
+    // from being published to the other warps, so its dependents in later
+    // tickets run into the limit and report SPTRSV_ERR_TIMEOUT
+    const SpinPolicy sp{env_value("SPTRSV_SPIN_LIMIT", 1ll << 24), 256, 128};
+    const long long wh = env_value("SPTRSV_DEBUG_NOALLOC_WITHHOLD", -1);
+    const int withhold = wh >= 0 && wh < n ? (int)wh : -1;
     const bool f64 = dtype == SPTRSV_F64;
     const bool upper = uplo == SPTRSV_UPPER;
     const bool unit = diag == SPTRSV_UNIT;
@@ -307,9 +346,9 @@ extern "C" SPTRSV_API sptrsv_status_t sptrsv_solve_noalloc(
     int lanes = 1;
     while (lanes < 32 && lanes * kChunk < off) lanes <<= 1;
     cudaError_t e = f64 ? launch_t<double>(lanes, n, d_rowptr, d_colidx, d_vals, upper, unit, d_b,
-                                           d_x, scratch, num_sms, s)
+                                           d_x, scratch, dev, num_sms, sp, withhold, s)
                         : launch_t<float>(lanes, n, d_rowptr, d_colidx, d_vals, upper, unit, d_b,
-                                          d_x, scratch, num_sms, s);
+                                          d_x, scratch, dev, num_sms, sp, withhold, s);
     if (e != cudaSuccess) return SPTRSV_ERR_CUDA;
     if (!error_row) return SPTRSV_OK;
     unsigned long long h = kStatusClear;

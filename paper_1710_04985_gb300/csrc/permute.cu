@@ -34,12 +34,18 @@ cudaError_t launch_ordered_lengths(int n, const int* ptr, const int* jlev, int* 
 
 // One warp per position k; lanes stride over the row's entries, so long rows
 // are copied with coalesced loads and stores.  pidx == nullptr refreshes the
-// values only.
+// values only.  diag >= 0 (a matrix with a stored, used diagonal; 1: the
+// diagonal is a row's first entry, 0: its last) stores the row pre-scaled
+// as the self-scheduled kernels use it: 1/d(i) in the diagonal's slot and
+// a_ij * (1/d(i)) for the other entries.  The kernels then skip the
+// division and the scaling, and since both are the same IEEE operations
+// they would do themselves, the results stay bitwise those of the unscaled
+// form.
 template <typename T>
 __global__ void permute_rows_k(int n, const int* __restrict__ ptr, const int* __restrict__ idx,
                                const int* __restrict__ vmap, const T* __restrict__ vals,
                                const int* __restrict__ jlev, const int* __restrict__ ipos,
-                               const int* __restrict__ pptr, int* pidx, T* pvals) {
+                               const int* __restrict__ pptr, int* pidx, T* pvals, int diag) {
     const int lane = threadIdx.x & 31;
     const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long k = (((long long)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5); k < n;
@@ -47,10 +53,17 @@ __global__ void permute_rows_k(int n, const int* __restrict__ ptr, const int* __
         const int i = jlev[k];
         const int beg = ptr[i], len = ptr[i + 1] - beg;
         const int out = pptr[k];
+        T dinv = T(1);
+        int qd = -1;
+        if (diag >= 0 && len > 0) {
+            qd = diag ? beg : beg + len - 1;
+            dinv = T(1) / vals[vmap ? vmap[qd] : qd];
+        }
         for (int e = lane; e < len; e += 32) {
             const int q = beg + e;
             if (pidx) pidx[out + e] = ipos[idx[q]];
-            pvals[out + e] = vals[vmap ? vmap[q] : q];
+            const T v = vals[vmap ? vmap[q] : q];
+            pvals[out + e] = diag < 0 ? v : (q == qd ? dinv : v * dinv);
         }
     }
 }
@@ -58,17 +71,17 @@ __global__ void permute_rows_k(int n, const int* __restrict__ ptr, const int* __
 cudaError_t launch_permute_rows(bool f64, int n, const int* ptr, const int* idx, const int* vmap,
                                 const void* vals, const int* jlev, const int* ipos,
                                 const int* pptr, int* pidx, void* pvals, int grid,
-                                cudaStream_t s) {
+                                cudaStream_t s, int diag) {
     if (n <= 0) return cudaSuccess;
     long long want = ((long long)n + 7) / 8;  // 8 warps of 256 threads per block
     int g = (int)(want < grid ? want : grid);
     if (g < 1) g = 1;
     if (f64)
         permute_rows_k<double><<<g, 256, 0, s>>>(n, ptr, idx, vmap, (const double*)vals, jlev,
-                                                ipos, pptr, pidx, (double*)pvals);
+                                                ipos, pptr, pidx, (double*)pvals, diag);
     else
         permute_rows_k<float><<<g, 256, 0, s>>>(n, ptr, idx, vmap, (const float*)vals, jlev,
-                                               ipos, pptr, pidx, (float*)pvals);
+                                               ipos, pptr, pidx, (float*)pvals, diag);
     return cudaGetLastError();
 }
 

@@ -109,6 +109,7 @@ __global__ void __launch_bounds__(1024) blocked_solve_k1(SolveParams p, int tile
     T* xs = (T*)blocked_smem;
     __shared__ int s_tile;
     __shared__ int s_next;
+    __shared__ long long s_pst[CS];  // first position of each tile of the cluster's group
     const unsigned crank = CS > 1 ? cluster_rank() : 0u;
     constexpr int R = 32 / W;
     constexpr int E = kChunk;
@@ -122,33 +123,39 @@ __global__ void __launch_bounds__(1024) blocked_solve_k1(SolveParams p, int tile
     T* x = (T*)p.x;
     T* xp = (T*)p.xp;  // publication buffer, position order
     const int n = p.n;
+    // First position of tile j (tiles of tile_rows positions, or the part
+    // boundaries of p.part_ptr); n past the last tile.
+    auto tile_start = [&](long long j) -> long long {
+        if (p.part_ptr) return j < p.nparts ? (long long)p.part_ptr[j] : (long long)n;
+        const long long q = j * tile_rows;
+        return q < n ? q : (long long)n;
+    };
     while (true) {
         long long p0, g0 = 0;  // this block's tile, and its group's first position
+        int in_tile;
         if (CS == 1) {
             if (threadIdx.x == 0) {
                 s_tile = atomicAdd(p.ticket, 1);
                 s_next = 0;
             }
             __syncthreads();
-            p0 = (long long)s_tile * tile_rows;
+            p0 = tile_start(s_tile);
             if (p0 >= n) break;
+            in_tile = (int)(tile_start((long long)s_tile + 1) - p0);
         } else {
             if (crank == 0 && threadIdx.x == 0) s_tile = atomicAdd(p.ticket, 1);
             cluster_sync();
-            const int t = crank == 0 ? s_tile : ld_cluster_int(cluster_addr(&s_tile, 0));
-            g0 = (long long)t * CS * tile_rows;
-            p0 = g0 + (long long)crank * tile_rows;
+            const long long t = crank == 0 ? s_tile : ld_cluster_int(cluster_addr(&s_tile, 0));
+            g0 = tile_start(t * CS);
+            p0 = tile_start(t * CS + crank);
+            in_tile = (int)(tile_start(t * CS + crank + 1) - p0);
+            if (threadIdx.x < CS) s_pst[threadIdx.x] = tile_start(t * CS + threadIdx.x);
             if (threadIdx.x == 0) s_next = 0;
-            if (p0 < n) {
-                const int m = (int)((n - p0) < tile_rows ? (n - p0) : tile_rows);
-                for (int k = threadIdx.x; k < m; k += blockDim.x)
-                    xs[k] = Marker<T>::pending_value();
-            }
+            for (int k = threadIdx.x; k < in_tile; k += blockDim.x)
+                xs[k] = Marker<T>::pending_value();
             cluster_sync();
             if (g0 >= n) break;  // the same for the whole cluster
         }
-        const int in_tile =
-            p0 >= n ? 0 : (int)((n - p0) < tile_rows ? (n - p0) : tile_rows);
         if (CS == 1)
             for (int k = threadIdx.x; k < in_tile; k += blockDim.x)
                 xs[k] = Marker<T>::pending_value();
@@ -179,13 +186,13 @@ __global__ void __launch_bounds__(1024) blocked_solve_k1(SolveParams p, int tile
                 if (sl == 0) {  // same arithmetic as the other self-scheduled forms
                     if (!p.unit) {
                         const int q = p.diag_first ? beg : end - 1;
-                        dinv = T(1) / vals[q];
+                        dinv = p.prescaled ? vals[q] : T(1) / vals[q];  // copy may hold 1/d(i)
                     }
                     sum = b[(long long)i * p.ldb];
                     if (!p.unit) sum *= dinv;
                 }
             }
-            if (W > 1 && !p.unit) dinv = __shfl_sync(FULL, dinv, grp * W);
+            if (W > 1 && !p.unit && !p.prescaled) dinv = __shfl_sync(FULL, dinv, grp * W);
             int q0 = beg + sl;
             // position of the dependency, its offset in the tile, or (remote)
             // its address in another block's shared memory
@@ -214,9 +221,12 @@ __global__ void __launch_bounds__(1024) blocked_solve_k1(SolveParams p, int tile
                                 c[e] = (int)(cc - p0);
                                 local |= 1u << e;
                             } else if (CS > 1 && cc >= g0) {
-                                const long long o = cc - g0;
-                                c[e] = (int)cluster_addr(xs + (int)(o % tile_rows),
-                                                         (unsigned)(o / tile_rows));
+                                // the earlier tile of the group that holds cc
+                                unsigned r = 0;
+#pragma unroll
+                                for (int j = 1; j < CS; ++j)
+                                    if (j < (int)crank && s_pst[j] <= cc) r = (unsigned)j;
+                                c[e] = (int)cluster_addr(xs + (int)(cc - s_pst[r]), r);
                                 remote |= 1u << e;
                             } else {
                                 c[e] = cc;
@@ -229,7 +239,7 @@ __global__ void __launch_bounds__(1024) blocked_solve_k1(SolveParams p, int tile
                     if (!(live & (1u << e))) continue;
                     v[e] = poll(e);
                 }
-                if (!p.unit) {
+                if (!p.unit && !p.prescaled) {
 #pragma unroll
                     for (int e = 0; e < E; ++e)
                         if (live & (1u << e)) a[e] *= dinv;
@@ -247,7 +257,10 @@ __global__ void __launch_bounds__(1024) blocked_solve_k1(SolveParams p, int tile
                 else
                     sts_volatile(xs + off, xi);
                 st_relaxed(xp + k, xi);
-                x[(long long)i * p.ldx] = xi;
+                if (p.xacc)
+                    accumulate_published(p, i, 0, xi);
+                else
+                    x[(long long)i * p.ldx] = xi;
             };
             bool lane_done = q0 >= end;
             if (!lane_done) load_chunk();
@@ -274,15 +287,7 @@ __global__ void __launch_bounds__(1024) blocked_solve_k1(SolveParams p, int tile
                 const bool fresh = !published && (done & gmask) == gmask;
                 if (__any_sync(FULL, fresh)) {
                     const T tot = group_sum<W>(sum, FULL);
-                    if (fresh && sl == 0 && i != p.withhold) {
-                        const T xi = publishable(tot);
-                        if (CS > 1)
-                            st_cluster(xs + off, xi);
-                        else
-                            sts_volatile(xs + off, xi);
-                        st_relaxed(xp + k, xi);
-                        x[(long long)i * p.ldx] = xi;
-                    }
+                    if (fresh && sl == 0 && i != p.withhold) publish_row(tot);
                 }
                 published = published || fresh;
                 if (__all_sync(FULL, published)) break;
@@ -363,7 +368,7 @@ static cudaError_t blocked_attrs() {
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(blocked_solve_k1<T, W, CS>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 64);
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 128);
     if (e == cudaSuccess) done |= bit;
     return e;
 }

@@ -37,7 +37,12 @@ __device__ __forceinline__ void mrhs_row_level(const SolveParams& p, int i, int 
     }
 }
 
-template <typename T, int W, bool MAP, bool SELF>
+// PERM: the pattern is the plan's level-ordered copy (position k = row
+// jlev[k], columns renumbered to positions, values pre-scaled for a non-unit
+// matrix); columns publish to the position-ordered buffer p.xp ([n][nrhs])
+// that waiting lanes poll, so a level's unknowns are one contiguous run, and
+// are stored to x (or added to p.xacc) for the caller.
+template <typename T, int W, bool MAP, bool SELF, bool PERM = false>
 __global__ void __launch_bounds__(1024) solve_mrhs_k(SolveParams p) {
     constexpr unsigned FULL = 0xffffffffu;
     constexpr int E = kChunk;
@@ -53,6 +58,8 @@ __global__ void __launch_bounds__(1024) solve_mrhs_k(SolveParams p) {
     const T* __restrict__ vals = (const T*)p.vals;
     const T* b = (const T*)p.b;
     T* x = (T*)p.x;
+    T* xpub = PERM ? (T*)p.xp : x;  // the array columns publish to and wait on
+    const long long ldp = PERM ? p.nrhs : p.ldx;
     int t = 0;
     if (lane == 0) t = atomicAdd(p.ticket, 1);
     t = __shfl_sync(FULL, t, 0);
@@ -64,15 +71,20 @@ __global__ void __launch_bounds__(1024) solve_mrhs_k(SolveParams p) {
         T dinv = T(1);
         int col = sl;
         bool lane_done = k >= p.n || col >= p.nrhs;
+        // the row's identity in the pattern: its own column index
+        const int self_col = PERM ? (int)k : 0;
+        const long long pub = PERM ? k : 0;  // publication row in xpub
         if (k < p.n) {
             i = p.jlev[k];
-            beg = p.ptr[i];
-            end = p.ptr[i + 1];
+            beg = p.ptr[PERM ? k : i];
+            end = p.ptr[(PERM ? k : i) + 1];
             if (!p.unit) {  // computed while the dependencies are pending
                 const int q = p.diag_first ? beg : end - 1;
-                dinv = T(1) / vals[MAP ? p.vmap[q] : q];
+                const T d = vals[MAP ? p.vmap[q] : q];
+                dinv = p.prescaled ? d : T(1) / d;  // a pre-scaled copy holds 1/d(i)
             }
         }
+        const long long prow = PERM ? pub : (long long)i;
         // per-lane state: column `col`, next entry q0, chunk of E entries; the
         // row is scaled by 1/d(i) so the column's value is the fold itself.
         int q0 = beg;
@@ -94,7 +106,7 @@ __global__ void __launch_bounds__(1024) solve_mrhs_k(SolveParams p) {
                 v[e] = T(0);
                 if (q < end) {
                     const int cc = p.idx[q];
-                    if (cc != i) {
+                    if (cc != (PERM ? self_col : i)) {
                         c[e] = cc;
                         a[e] = vals[MAP ? p.vmap[q] : q];
                         live |= 1u << e;
@@ -103,8 +115,8 @@ __global__ void __launch_bounds__(1024) solve_mrhs_k(SolveParams p) {
             }
 #pragma unroll
             for (int e = 0; e < E; ++e)
-                if (live & (1u << e)) v[e] = ld_relaxed(x + (long long)c[e] * p.ldx + col);
-            if (!p.unit) {
+                if (live & (1u << e)) v[e] = ld_relaxed(xpub + (long long)c[e] * ldp + col);
+            if (!p.unit && !p.prescaled) {
 #pragma unroll
                 for (int e = 0; e < E; ++e)
                     if (live & (1u << e)) a[e] *= dinv;
@@ -124,7 +136,14 @@ __global__ void __launch_bounds__(1024) solve_mrhs_k(SolveParams p) {
                 acc = fold_chunk(acc, a, v, live);
                 q0 += E;
                 if (q0 >= end) {  // column done: publish it, move to the next tile
-                    if (i != p.withhold) st_relaxed(x + (long long)i * p.ldx + col, publishable(acc));
+                    if (i != p.withhold) {
+                        const T val = publishable(acc);
+                        st_relaxed(xpub + prow * ldp + col, val);
+                        if (p.xacc)
+                            accumulate_published(p, i, col, val);
+                        else if (PERM)
+                            x[(long long)i * p.ldx + col] = val;
+                    }
                     col += W;
                     q0 = beg;
                     if (col >= p.nrhs) {
@@ -144,7 +163,7 @@ __global__ void __launch_bounds__(1024) solve_mrhs_k(SolveParams p) {
                 do {
 #pragma unroll
                     for (int e = 0; e < E; ++e)
-                        if (pend & (1u << e)) v[e] = ld_relaxed(x + (long long)c[e] * p.ldx + col);
+                        if (pend & (1u << e)) v[e] = ld_relaxed(xpub + (long long)c[e] * ldp + col);
 #pragma unroll
                     for (int e = 0; e < E; ++e)
                         if ((pend & (1u << e)) && !Marker<T>::pending(v[e])) pend &= ~(1u << e);
@@ -180,7 +199,9 @@ static cudaError_t mrhs_w(const SolveParams& p, int grid, int block, cudaStream_
         const long long threads = (long long)p.cnt * W;
         grid = (int)((threads + block - 1) / block);
     }
-    if (p.vmap)
+    if (SELF && p.xp)  // level-ordered copy: values gathered, no map
+        solve_mrhs_k<T, W, false, true, true><<<grid, block, 0, s>>>(p);
+    else if (p.vmap)
         solve_mrhs_k<T, W, true, SELF><<<grid, block, 0, s>>>(p);
     else
         solve_mrhs_k<T, W, false, SELF><<<grid, block, 0, s>>>(p);

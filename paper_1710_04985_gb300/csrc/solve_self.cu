@@ -105,13 +105,14 @@ __global__ void __launch_bounds__(1024) self_solve_k1(SolveParams p) {
                 // remain once the last dependency arrives.
                 if (!p.unit) {
                     const int q = p.diag_first ? beg : end - 1;
-                    dinv = T(1) / vals[MAP ? p.vmap[q] : q];
+                    const T d = vals[MAP ? p.vmap[q] : q];
+                    dinv = p.prescaled ? d : T(1) / d;  // a pre-scaled copy holds 1/d(i)
                 }
                 sum = b[(long long)i * p.ldb];
                 if (!p.unit) sum *= dinv;
             }
         }
-        if (W > 1 && !p.unit) dinv = __shfl_sync(FULL, dinv, grp * W);
+        if (W > 1 && !p.unit && !p.prescaled) dinv = __shfl_sync(FULL, dinv, grp * W);
         // ---- per-lane chunk state: entries q0 + e*W, e < E
         int q0 = beg + sl;
         int c[E];
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(1024) self_solve_k1(SolveParams p) {
 #pragma unroll
             for (int e = 0; e < E; ++e)
                 if (live & (1u << e)) v[e] = ld_relaxed(xpub + (long long)c[e] * ldp);
-            if (!p.unit) {
+            if (!p.unit && !p.prescaled) {
 #pragma unroll
                 for (int e = 0; e < E; ++e)
                     if (live & (1u << e)) a[e] *= dinv;
@@ -150,7 +151,10 @@ __global__ void __launch_bounds__(1024) self_solve_k1(SolveParams p) {
         auto publish_row = [&](T tot) {
             const T val = publishable(tot);
             st_relaxed(xpub + (PERM ? k : (long long)i * p.ldx), val);
-            if (PERM) x[(long long)i * p.ldx] = val;
+            if (p.xacc)
+                accumulate_published(p, i, 0, val);
+            else if (PERM)
+                x[(long long)i * p.ldx] = val;
         };
         bool lane_done = q0 >= end;
         if (!lane_done) load_chunk();
@@ -177,11 +181,7 @@ __global__ void __launch_bounds__(1024) self_solve_k1(SolveParams p) {
             const bool fresh = !published && (done & gmask) == gmask;
             if (__any_sync(FULL, fresh)) {  // FP64 is scarce on GB300: reduce only then
                 const T tot = group_sum<W>(sum, FULL);
-                if (fresh && sl == 0 && i != p.withhold) {
-                    const T val = publishable(tot);
-                    st_relaxed(xpub + (PERM ? k : (long long)i * p.ldx), val);
-                    if (PERM) x[(long long)i * p.ldx] = val;
-                }
+                if (fresh && sl == 0 && i != p.withhold) publish_row(tot);
             }
             published = published || fresh;
             if (__all_sync(FULL, published)) break;

@@ -126,11 +126,26 @@ class TriangularPlan:
         return self._keep[2]
 
     # ------------------------------------------------------------ solves
-    best_algo = "self"   # set by autotune.tune_algos; used when algo="auto"
+    @property
+    def best_algo(self):
+        """The form ``algo="auto"`` and the FP32 solves of ``solve_refined``
+        run: the plan's default algorithm in the library (set by the
+        autotuner; "self" until then)."""
+        a = ctypes.c_int()
+        check(_lib.load().sptrsv_get_default_algo(self._h, ctypes.byref(a)),
+              "sptrsv_get_default_algo")
+        return {v: k for k, v in ALGOS.items()}[a.value]
+
+    @best_algo.setter
+    def best_algo(self, name):
+        check(_lib.load().sptrsv_set_default_algo(self._h, ALGOS[name]),
+              "sptrsv_set_default_algo")
+
+    best_algo_mrhs = "self"   # the multi-RHS form of algo="auto" (set by the autotuner)
 
     def _solve(self, fn, name, b, out, algo, stream):
         if algo == "auto":
-            algo = self.best_algo
+            algo = self.best_algo if b.dim() == 1 or b.shape[1] == 1 else self.best_algo_mrhs
         if b.dtype != self.dtype or b.device != self.device:
             raise ValueError(f"{name}: b must be {self.dtype} on {self.device}")
         if out is None:
@@ -160,6 +175,18 @@ class TriangularPlan:
     def prepare_transpose(self, stream=None):
         check(_lib.load().sptrsv_prepare_transpose(self._h, _stream_handle(stream)),
               "sptrsv_prepare_transpose")
+
+    def prepare(self, algo="auto", transpose=False, stream=None):
+        """Build what the first solve of ``algo`` would build (copies,
+        transposed pattern, segment order); synchronises.  Returns the host
+        wall time in ms."""
+        import time
+        if algo == "auto":
+            algo = self.best_algo
+        t0 = time.perf_counter()
+        check(_lib.load().sptrsv_prepare(self._h, int(bool(transpose)), ALGOS[algo],
+                                         _stream_handle(stream)), "sptrsv_prepare")
+        return 1e3 * (time.perf_counter() - t0)
 
     def grad_vals(self, y, x, out=None, stream=None):
         """-y_i . x_j on every stored (i, j): dloss/dA given y = A^{-T} dloss/dx."""
@@ -287,6 +314,22 @@ class TriangularPlan:
         check(_lib.load().sptrsv_get_partition(self._h, ctypes.byref(v), ctypes.byref(c)),
               "sptrsv_get_partition")
         return v.value, c.value
+
+    def partition_info(self, transpose=False):
+        """Layout of the partitioned solve's copy (after a partitioned solve in
+        that direction): dict(nparts, nblocks, max_part_rows, part_ptr, order)
+        with part_ptr[nparts + 1] the first position of every part in
+        hand-out order and order[n] the row at every position."""
+        np_, nb, mx = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        pp, od = ctypes.c_void_p(), ctypes.c_void_p()
+        check(_lib.load().sptrsv_partition_info(self._h, int(bool(transpose)),
+                                                ctypes.byref(np_), ctypes.byref(nb),
+                                                ctypes.byref(mx), ctypes.byref(pp),
+                                                ctypes.byref(od)), "sptrsv_partition_info")
+        torch.cuda.synchronize(self.device)
+        return {"nparts": np_.value, "nblocks": nb.value, "max_part_rows": mx.value,
+                "part_ptr": _dev_int_array(pp.value, np_.value + 1 if self.n else 0, self.device),
+                "order": _dev_int_array(od.value, self.n, self.device)}
 
     def set_spin_limit(self, polls):
         check(_lib.load().sptrsv_set_spin_limit(self._h, int(polls)), "sptrsv_set_spin_limit")

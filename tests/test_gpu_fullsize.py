@@ -168,18 +168,30 @@ def test_workload3_batch_of_512_systems(cuda_device):
     """512 independent general systems, n log-uniform in [1k, 64k], solved by
     one graph-replayed launch of the autotuned plan; every system checked
     against its own oracle solve, and the block-diagonal levels against the
-    per-system levels."""
+    per-system levels.  Then the same batch on the partitioned form (the
+    system boundaries found by the plan: one independent block per system)
+    and by FP32 solves with FP64 refinement, both against the oracle."""
     from paper_1710_04985_gb300 import BatchedTriangularSolve
     mats = synth.batch_general_parallel(512, synth.SEED_BASE + 3)
     bs = BatchedTriangularSolve([(m.rowptr, m.colidx, m.vals) for m in mats], tune=True)
     bvec = [synth.uniform(m.n, 7000 + s) for s, m in enumerate(mats)]
-    x = bs.solve(torch.tensor(np.concatenate(bvec), device=dev())).cpu().numpy()
+    bt = torch.tensor(np.concatenate(bvec), device=dev())
+    x = bs.solve(bt).cpu().numpy()
     lev = bs.plan.levels()["lev"].cpu().numpy()
     off = bs.offsets
-    worst = 0.0
+    refs = [oracle.solve(m.rowptr, m.colidx, m.vals, bvec[s]) for s, m in enumerate(mats)]
+
+    def worst(xs):
+        return max(relerr(xs[off[s]:off[s + 1]], refs[s]) for s in range(len(mats)))
+
     for s, m in enumerate(mats):
-        ref = oracle.solve(m.rowptr, m.colidx, m.vals, bvec[s])
-        worst = max(worst, relerr(x[off[s]:off[s + 1]], ref))
         lref, _ = oracle.levels(m.rowptr, m.colidx)
         assert np.array_equal(lev[off[s]:off[s + 1]], lref)
-    assert worst <= TOL64
+    assert worst(x) <= TOL64
+    xp = bs.plan.solve(bt, algo="partitioned").cpu().numpy()
+    assert worst(xp) <= TOL64
+    assert bs.plan.partition_info()["nblocks"] == 512
+    xr, iters, rel = bs.solve_refined(bt)
+    assert 1 <= iters <= 10
+    assert worst(xr.cpu().numpy()) <= TOL64
+    assert bs.plan.status() == (0, -1)

@@ -228,15 +228,27 @@ def test_per_algorithm_launch_shape():
 
 
 @pytest.mark.parametrize("k", [2, 3, 8, 32, 33])
-@pytest.mark.parametrize("algo", ["self", "level", "tiled", "chains"])
+@pytest.mark.parametrize("algo", ["self", "level", "tiled", "chains", "permuted", "blocked",
+                                  "partitioned"])
 def test_multi_rhs(k, algo):
-    for name in ("general", "ilu_U"):
+    """Every form takes several right-hand sides: the copying forms run the
+    multi-RHS kernel on the level-ordered copy (bitwise equal to the
+    in-place multi-RHS kernel: same width, same fold order per column), the
+    others the in-place or level-scheduled multi-RHS kernel."""
+    for name in ("general", "ilu_U", "ilu_L"):
         A = mat(name)
         b = synth.uniform((A.n, k), 14 + k)
         ref = oracle.solve(A.rowptr, A.colidx, A.vals, b, upper=A.upper, unit=A.unit)
         with plan_for(A) as p:
-            x = p.solve(torch.tensor(b, device=dev()), algo=algo)
+            bt = torch.tensor(b, device=dev())
+            x = p.solve(bt, algo=algo)
             assert relerr(x, ref) <= TOL64
+            if algo in ("permuted", "blocked", "partitioned"):
+                assert torch.equal(x, p.solve(bt, algo="self"))
+                reft = oracle.solve_transpose(A.rowptr, A.colidx, A.vals, b, upper=A.upper,
+                                              unit=A.unit)
+                assert relerr(p.solve_transpose(bt, algo=algo), reft) <= TOL64
+            assert p.status() == (0, -1)
 
 
 def test_multi_rhs_width_does_not_change_results():
@@ -412,6 +424,38 @@ def test_autograd_sees_in_place_value_updates_with_copying_algorithms():
             x = sparse_triangular_solve(p, v, bt, algo=algo)
             ref = oracle.solve(A.rowptr, A.colidx, v.cpu().numpy(), b, unit=A.unit)
             assert relerr(x.detach(), ref) <= TOL64, algo
+
+
+def test_c_abi_in_place_value_update_needs_refresh():
+    """Through the C ABI: the default form (SPTRSV_ALGO_AUTO) is the
+    partitioned one, which solves from a snapshot of the values.  Rewriting
+    d_vals in place leaves the snapshot stale until sptrsv_refresh_values;
+    after it the solve matches the oracle on the new values."""
+    import ctypes
+
+    from paper_1710_04985_gb300 import _lib
+    lib = _lib.load()
+    A = mat("general")
+    b = synth.uniform(A.n, 61)
+    with plan_for(A) as p:
+        h = p._h
+        s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        bt = torch.tensor(b, device=dev())
+        x = torch.empty_like(bt)
+
+        def solve_auto():
+            assert lib.sptrsv_solve(h, ctypes.c_void_p(bt.data_ptr()),
+                                    ctypes.c_void_p(x.data_ptr()), 1, 1, _lib.ALGO_AUTO, s) == 0
+            return x.clone()
+
+        assert lib.sptrsv_set_default_algo(h, _lib.ALGO_SELF_PARTITIONED) == 0
+        x0 = solve_auto()
+        assert relerr(x0, oracle.solve(A.rowptr, A.colidx, A.vals, b)) <= TOL64
+        p.vals.mul_(1.5)                                  # in place: same pointer
+        assert torch.equal(solve_auto(), x0)              # the snapshot is stale
+        assert lib.sptrsv_refresh_values(h, s) == 0
+        ref = oracle.solve(A.rowptr, A.colidx, 1.5 * A.vals, b)
+        assert relerr(solve_auto(), ref) <= TOL64
 
 
 @pytest.mark.parametrize("algo", ["permuted", "partitioned"])
@@ -634,15 +678,31 @@ def test_autograd_against_oracle_and_finite_differences(transpose):
 
 @pytest.mark.parametrize("name", ["general", "ilu_L", "ilu_U", "long_rows"])
 @pytest.mark.parametrize("k", [1, 8])
-def test_fp32_with_fp64_refinement(name, k):
+@pytest.mark.parametrize("algo", ["self", "partitioned", "permuted", "blocked", "chains",
+                                  "level"])
+def test_fp32_with_fp64_refinement(name, k, algo):
+    """The FP32 solves run the plan's default form: the in-place and copying
+    forms add each correction into x as they publish it, the others through
+    an update pass; every way reaches the FP64 oracle within 1e-12."""
     A = mat(name)
     b = synth.uniform((A.n, k) if k > 1 else A.n, 27)
     ref = oracle.solve(A.rowptr, A.colidx, A.vals, b, upper=A.upper, unit=A.unit)
     with plan_for(A) as p:
+        p.best_algo = algo
+        p.set_partition(1024, 2)
         x, iters, rel = p.solve_refined(torch.tensor(b, device=dev()))
         err = relerr(x, ref)
         assert err <= TOL64, (err, iters, rel)
         assert 1 <= iters <= 10
+        assert p.status() == (0, -1)
+        if algo == "partitioned" and k == 1:
+            # the FP32 copy follows value updates (refresh), like the FP64 one
+            v2 = torch.tensor(A.vals * 1.25, device=dev())
+            p.set_values(v2)
+            ref2 = oracle.solve(A.rowptr, A.colidx, A.vals * 1.25, b, upper=A.upper,
+                                unit=A.unit)
+            x2, _, _ = p.solve_refined(torch.tensor(b, device=dev()))
+            assert relerr(x2, ref2) <= TOL64
 
 
 # ---------------------------------------------------------------- batching
