@@ -176,9 +176,10 @@ void oracle_residual(int n, const int *rowptr, const int *colidx,
             double s = b[(size_t)i * ldb + c];
             for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
                 int j = colidx[p];
-                double a = (j == i && unit) ? 1.0 : vals[p];
-                s -= a * x[(size_t)j * ldx + c];
+                if (unit && j == i) continue;   /* a stored diagonal is ignored ... */
+                s -= x[(size_t)j * ldx + c] * vals[p];
             }
+            if (unit) s -= x[(size_t)i * ldx + c];   /* ... and 1 is used, stored or not */
             r[(size_t)i * ldr + c] = s;
         }
     }

@@ -45,8 +45,10 @@ MUTATIONS = {
     "gradient_operands_transposed": (
         "s += y[(size_t)i * ldy + c] * x[(size_t)j * ldx + c];",
         "s += y[(size_t)j * ldy + c] * x[(size_t)i * ldx + c];"),
-    "residual_ignores_unit_diagonal": ("double a = (j == i && unit) ? 1.0 : vals[p];",
-                                       "double a = vals[p];"),
+    "residual_drops_unit_diagonal": ("if (unit) s -= x[(size_t)i * ldx + c];", ""),
+    "residual_sign_flipped": ("s -= x[(size_t)j * ldx + c] * vals[p];",
+                              "s += x[(size_t)j * ldx + c] * vals[p];"),
+    "residual_uses_stored_unit_diagonal": ("if (unit && j == i) continue;", ""),
 }
 
 PIN_CHECKS = [

@@ -388,3 +388,13 @@ def test_residual_matches_scipy():
     bb = synth.times_vector(L, xx)
     r = oracle.residual(L2.rowptr, L2.colidx, L2.vals, bb, xx, unit=True)
     assert np.max(np.abs(r)) <= 1e-14
+    # a unit diagonal that is not stored still counts as 1 (the unit flag's
+    # reading): r = b - (strict lower part + I) x
+    rows = A.row_of_entries()
+    off = rows != A.colidx
+    S = sp.csr_matrix((A.vals[off], (rows[off], A.colidx[off])), shape=(A.n, A.n))
+    rp = np.zeros(A.n + 1, dtype=np.int32)
+    np.cumsum(np.bincount(rows[off], minlength=A.n), out=rp[1:])
+    want = b - (S + sp.identity(A.n)) @ x
+    got = oracle.residual(rp, A.colidx[off].astype(np.int32), A.vals[off], b, x, unit=True)
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12)
