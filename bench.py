@@ -24,6 +24,7 @@ import os
 import re
 import statistics
 import subprocess
+import threading
 import sys
 import time
 
@@ -100,44 +101,64 @@ def ncu_traffic(sha, algo="self"):
 
 
 class ClockSampler:
-    """nvidia-smi samples during the timed region."""
+    """nvidia-smi samples (every 100 ms) stamped on arrival with the host clock,
+    so that a summary can be taken over any window: the timed region alone, or
+    the whole measured phase (timed region, end-to-end and the other workloads).
+    The sampler is live before the caller's first window opens."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
+        self.rows = []
+        self.thread = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            r = next(csv.reader([line]), [])
+            if len(r) >= 9:
+                self.rows.append((time.monotonic(), r))
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+            return self
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        t_end = time.monotonic() + 5.0
+        while not self.rows and time.monotonic() < t_end and self.proc.poll() is None:
+            time.sleep(0.01)
         return self
 
     def __exit__(self, *exc):
-        self.out = ""
         if self.proc is not None:
             self.proc.terminate()
             try:
-                self.out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
-                self.out, _ = self.proc.communicate()
+                self.proc.wait()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
 
-    def summary(self):
-        rows = [r for r in csv.reader(io.StringIO(self.out or "")) if len(r) >= 9]
+    def summary(self, t0=None, t1=None, exclude=()):
+        rows = [r for t, r in list(self.rows)
+                if (t0 is None or t >= t0) and (t1 is None or t <= t1)
+                and not any(a <= t <= b for a, b in exclude)]
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows for k in range(4)
+        reasons = sorted({self.NAMES[k] for r in rows for k in range(4)
                           if r[5 + k].strip().lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
@@ -246,10 +267,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-compare", action="store_true")
-    ap.add_argument("--single-solve", choices=["L", "U", "G"], default=None,
+    ap.add_argument("--single-solve", choices=["L", "U", "G", "B"], default=None,
                     help="profiling target: build one plan (L or U factor of the 128^3 "
-                         "ILU(0) workload, or the n = 10^6 general matrix), apply "
-                         "--lanes/--max-blocks/--algo and run --repeat solves, nothing else")
+                         "ILU(0) workload, the n = 10^6 general matrix, or the 512-system "
+                         "batch), apply --lanes/--max-blocks/--algo and run --repeat "
+                         "solves (--refined: refined solves), nothing else")
+    ap.add_argument("--refined", action="store_true",
+                    help="--single-solve: FP32 + FP64 refined solves instead")
     ap.add_argument("--lanes", type=int, default=4)
     ap.add_argument("--max-blocks", type=int, default=304)
     ap.add_argument("--algo", default="self",
@@ -351,12 +375,14 @@ def main():
     pl.profile_read()
     pu.profile_read()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        e0.record()
-        for _ in range(args.steps):
-            step()
-        e1.record()
-        torch.cuda.synchronize()
+    clk = ClockSampler(local).__enter__()   # closed after the other workloads
+    tt0 = time.monotonic()
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    tt1 = time.monotonic()
     if pg:
         pg.barrier()
     ms = e0.elapsed_time(e1)
@@ -525,12 +551,21 @@ def main():
             extra["speedup_vs_cusparse"] = extra["cusparse_spsv"]["ms_per_step"] / self_ms
 
     cpu, refs = None, None
+    tc0 = tc1 = time.monotonic()
     if rank == 0 and args.cpu_seconds > 0:
         cpu, refs = cpu_leg(L, U, b_host, W, args.cpu_seconds)
+        tc1 = time.monotonic()
     if W is not None:
         t_hop = (extra["latency_bound"]["t_hop_us"] if "latency_bound" in extra
                  else chain_latency(dev, [382], kernel_avg_ms)["t_hop_us"])
         extra.update(secondary(dev, W, refs, min(t_hop.values()), peak, pl, L))
+
+    clk.__exit__(None, None, None)
+    clocks = clk.summary(tt0 - 0.1, tt1 + 0.1)
+    clocks["window"] = "timed region +- 100 ms (one sample period)"
+    clocks["measured_phase"] = clk.summary(exclude=[(tc0, tc1)])
+    clocks["measured_phase"]["window"] = ("timed region, end-to-end, comparisons and the "
+                                          "other workloads (not the host-only oracle leg)")
 
     if rank == 0:
         line = {
@@ -577,7 +612,7 @@ def main():
                     "serial_value": 2 * e2e_steps * world / e2e_serial_s,
                     "serial_max_rel_err": e2e_serial_err},
             "gpu_launches": launches,
-            "clocks": clk.summary(),
+            "clocks": clocks,
             "analysis_ms": setup,
             "max_rel_err_vs_xtrue": err,
         }
@@ -598,6 +633,11 @@ def single_solve(args):
     dev = torch.device("cuda", 0)
     if args.single_solve == "G":
         A, xt, bh = synth.workload2()
+    elif args.single_solve == "B":
+        mats = synth.batch_general_parallel(512, synth.SEED_BASE + 3)
+        A = synth.block_diagonal(mats)
+        xt = np.concatenate([synth.uniform(m.n, 7000 + s) for s, m in enumerate(mats)])
+        bh = synth.times_vector(A, xt)
     else:
         L, U, xt, bL, bU = synth.workload1()
         A, bh = (L, bL) if args.single_solve == "L" else (U, bU)
@@ -607,8 +647,14 @@ def single_solve(args):
     p.set_partition(args.part_rows, args.cluster)
     b = torch.tensor(bh, device=dev)
     x = torch.empty_like(b)
+    if args.refined:
+        p.set_algo_tuning("permuted", args.lanes, args.block, args.max_blocks)
+        p.best_algo = args.algo
     for _ in range(args.repeat):
-        p.solve(b, out=x, algo=args.algo)
+        if args.refined:
+            p.solve_refined(b, out=x)
+        else:
+            p.solve(b, out=x, algo=args.algo)
     torch.cuda.synchronize()
     err = float(np.max(np.abs(x.cpu().numpy() - xt)) / np.max(np.abs(xt)))
     print(json.dumps({"single_solve": args.single_solve, "algo": args.algo, "lanes": args.lanes,
@@ -934,11 +980,12 @@ def secondary(dev, W, refs, t_hop_us, peak, pl, L):
                        "algo": form, "lanes_per_row": lanes}
     res["multi_rhs_ilu_L"] = mr
 
-    # ---- FP32 bulk solves + FP64 refinement
+    # ---- FP32 bulk solves + FP64 refinement (the faster of the two forms)
     ir = {}
     for name, p, A2 in (("ilu_L", pl, L), ("general_1M", gen_plan, A)):
         b2 = torch.tensor(W["refine_b"][name], device=dev)
         out = torch.empty_like(b2)
+        forms = autotune.tune_refine(p, b2)
         p.solve_refined(b2, out=out)
         torch.cuda.synchronize()
         reps = 5
@@ -949,11 +996,12 @@ def secondary(dev, W, refs, t_hop_us, peak, pl, L):
         ms = (time.perf_counter() - t0) / reps * 1e3
         f64_ms = _events_ms(lambda: p.solve(b2, algo="auto"), 5)
         r = {"ms": ms, "corrections": iters, "final_rel_residual": rel,
-             "fp32_form": p.best_algo, "plain_fp64_solve_ms": f64_ms,
-             "vs_plain_fp64": ms / f64_ms,
-             "how": "host wall clock around the call (it reads the residual norm once per "
-                    "step); FP32 solves of the tuned form, corrections added into x as they "
-                    "are published, one FP64 residual pass per step"}
+             "form": forms["mode"], "ms_by_form": forms["ms"], "fp32_form": p.best_algo,
+             "plain_fp64_solve_ms": f64_ms, "vs_plain_fp64": ms / f64_ms,
+             "how": "host wall clock around the call; staged: an FP32 solve pass of the "
+                    "tuned form (corrections added into x as published) and an FP64 "
+                    "residual pass per step; one_pass: every step in one self-scheduled "
+                    "sweep over the level-ordered copy"}
         if ref("refine_" + name) is not None:
             r["max_rel_err_vs_fp64_oracle"] = _relerr(out, ref("refine_" + name))
         ir[name] = r
@@ -1010,13 +1058,15 @@ def secondary(dev, W, refs, t_hop_us, peak, pl, L):
                       "max_part_rows": info["max_part_rows"]}
     if ref("batch") is not None:
         r["max_rel_err_vs_oracle"] = _relerr(xb, ref("batch"))
+    forms = autotune.tune_refine(bs.plan, bdev, reps=1)
     bs.solve_refined(bdev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     xr, iters, rel = bs.solve_refined(bdev)
     torch.cuda.synchronize()
     r["refined"] = {"ms": 1e3 * (time.perf_counter() - t0), "corrections": iters,
-                    "final_rel_residual": rel, "fp32_form": bs.plan.best_algo}
+                    "final_rel_residual": rel, "form": forms["mode"],
+                    "ms_by_form": forms["ms"], "fp32_form": bs.plan.best_algo}
     if ref("batch") is not None:
         r["refined"]["max_rel_err_vs_fp64_oracle"] = _relerr(xr, ref("batch"))
     r["wall_s"] = time.perf_counter() - t_start

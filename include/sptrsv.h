@@ -171,6 +171,19 @@ typedef enum {
                                      autotuner measured fastest                          */
 } sptrsv_algo_t;
 
+/* How sptrsv_solve_refined runs the refinement of one right-hand side
+ * (several right-hand sides always use the staged form). */
+typedef enum {
+    SPTRSV_REFINE_STAGED = 0,    /* default: one FP32 solve pass (the plan's default form)
+                                    and one FP64 residual pass per refinement step, the
+                                    residual norm read by the host after each step      */
+    SPTRSV_REFINE_ONE_PASS = 1   /* every step in one self-scheduled sweep over the
+                                    level-ordered copy: a row computes its residual and
+                                    correction for step m as soon as its dependencies
+                                    have published step m (faster on deep, narrow
+                                    matrices, slower on wide ones)                       */
+} sptrsv_refine_t;
+
 /* Level-analysis methods (sptrsv_reanalyze).  All give the same levels and
  * level sets (levels are unique); they differ in cost. */
 typedef enum {
@@ -305,14 +318,21 @@ SPTRSV_API sptrsv_status_t sptrsv_residual(sptrsv_plan_t plan, const double *d_b
 
 /* Mixed-precision solve with iterative refinement (F64 plans only; the
  * motivation is the refinement use of Sec. 1).  The bulk triangular solves
- * run in FP32 (an FP32 copy of the values, FP32 vectors and accumulation)
- * with the plan's default form (sptrsv_set_default_algo) and that form's
- * launch shape; the residual r = b - A x, the correction update x += d and
- * the solution are FP64.  The in-place, level-ordered, blocked and
- * partitioned forms add every correction into x as they publish it (no
- * separate update pass); each residual pass also writes the FP32 right-hand
- * side of the next correction.  Stops when
- * max|r| / (max|b| + ||A||_inf max|x|) <= tol or after max_iter corrections.
+ * run in FP32 (an FP32 copy of the values, FP32 vectors and accumulation);
+ * the residual r = b - A x, the correction update x += d and the solution
+ * are FP64.  Two forms (sptrsv_set_refine_mode):
+ *  - staged: FP32 solves of the plan's default form (sptrsv_set_default_algo)
+ *    in that form's launch shape; the in-place, level-ordered, blocked and
+ *    partitioned forms add every correction into x as they publish it (no
+ *    separate update pass); each residual pass also writes the FP32
+ *    right-hand side of the next correction;
+ *  - one pass (one right-hand side): every step in one self-scheduled sweep
+ *    over the level-ordered copy, in the level-ordered form's launch shape;
+ *    a first pass applies three corrections (the residual it measures last
+ *    is that of its next-to-last iterate), later passes start from the
+ *    current x.
+ * Stops when max|r| / (max|b| + ||A||_inf max|x|) <= tol or after max_iter
+ * corrections.
  *   d_b, d_x     device FP64 [n][ld]; x is overwritten (no initial guess)
  *   iters        out (nullable): corrections applied after the first solve
  *   rel_resid    out (nullable): the last relative residual measured
@@ -325,6 +345,11 @@ SPTRSV_API sptrsv_status_t sptrsv_solve_refined(sptrsv_plan_t plan, const double
                                      double *d_x, int nrhs, int ld,
                                      int max_iter, double tol, int *iters,
                                      double *rel_resid, void *stream);
+
+/* The refinement form of sptrsv_solve_refined for one right-hand side
+ * (SPTRSV_REFINE_STAGED by default); the getter returns it as an int. */
+SPTRSV_API sptrsv_status_t sptrsv_set_refine_mode(sptrsv_plan_t plan, sptrsv_refine_t mode);
+SPTRSV_API sptrsv_status_t sptrsv_get_refine_mode(sptrsv_plan_t plan, int *mode);
 
 /* The form SPTRSV_ALGO_AUTO and the FP32 solves of sptrsv_solve_refined
  * run (any algorithm but SPTRSV_ALGO_AUTO; SPTRSV_ALGO_SELF by default).

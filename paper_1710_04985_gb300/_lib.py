@@ -23,6 +23,7 @@ ERR_INTERNAL = 8
 
 ANALYSIS_SWEEP, ANALYSIS_KAHN_HOST_LOOP, ANALYSIS_KAHN_PERSISTENT, ANALYSIS_AUTO = 0, 1, 2, 3
 F64, F32 = 0, 1
+REFINE_STAGED, REFINE_ONE_PASS = 0, 1
 LOWER, UPPER = 0, 1
 NON_UNIT, UNIT = 0, 1
 (ALGO_LEVEL, ALGO_SELF, ALGO_SELF_TILED, ALGO_SELF_CHAINS, ALGO_SELF_PERMUTED,
@@ -46,6 +47,8 @@ SIGNATURES = [
     ("sptrsv_residual", _c_int, [_vp, _vp, _vp, _vp, _c_int, _c_int, _vp]),
     ("sptrsv_solve_refined", _c_int, [_vp, _vp, _vp, _c_int, _c_int, _c_int, _c_dbl, _ip, _dp, _vp]),
     ("sptrsv_set_default_algo", _c_int, [_vp, _c_int]),
+    ("sptrsv_set_refine_mode", _c_int, [_vp, _c_int]),
+    ("sptrsv_get_refine_mode", _c_int, [_vp, _ip]),
     ("sptrsv_get_default_algo", _c_int, [_vp, _ip]),
     ("sptrsv_set_values", _c_int, [_vp, _vp, _vp]),
     ("sptrsv_refresh_values", _c_int, [_vp, _vp]),

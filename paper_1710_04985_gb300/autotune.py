@@ -145,13 +145,13 @@ def _apply(plan, best, algo, nrhs=1):
 # so far, a few candidates each, for callers that tune several workloads in
 # one short run.
 QUICK = {
-    "self": dict(lanes=(1, 2, 4, 8), blocks=(256,), grids=(0, 2)),
-    "permuted": dict(lanes=(1, 2, 4), blocks=(256, 512), grids=(0,)),
+    "self": dict(lanes=(1, 4, 8, 16, 32), blocks=(256,), grids=(0, 2)),
+    "permuted": dict(lanes=(1, 2, 4, 16), blocks=(256, 512), grids=(0, 1)),
     "blocked": dict(lanes=(1, 4), blocks=(512, 1024), grids=(0,), tiles=(256, 2048)),
-    "partitioned": dict(lanes=(1, 2, 4), blocks=(256, 512), grids=(0,), tiles=(0, 8192, 16384),
-                        clusters=(4,)),
+    "partitioned": dict(lanes=(1, 2, 4, 8, 16), blocks=(512, 1024), grids=(0,),
+                        tiles=(0, 8192, 16384), clusters=(4,)),
     "tiled": dict(lanes=(1, 4), blocks=(256,), grids=(0,), tiles=(2048,), tile_orders=(False,)),
-    "chains": dict(lanes=(2, 4, 8), blocks=(256,), grids=(0,)),
+    "chains": dict(lanes=(8, 16, 32), blocks=(256,), grids=(0, 2)),
 }
 
 
@@ -218,3 +218,25 @@ def apply_choice(plan, ch):
     _apply(plan, best, algo)
     plan.best_algo = algo
     return {"algo": algo, "best": best, "per_algo": {}}
+
+
+def tune_refine(plan, b, reps=2):
+    """Time ``plan.solve_refined(b)`` in both refinement forms (with the
+    plan's current tuning), keep the faster one on the plan and return
+    ``{"mode": name, "ms": {mode: ms}}``.  One right-hand side only (several
+    always refine in the staged form)."""
+    import time
+    out = torch.empty_like(b)
+    ms = {}
+    for mode in ("staged", "one_pass"):
+        plan.refine_mode = mode
+        plan.solve_refined(b, out=out)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            plan.solve_refined(b, out=out)
+        torch.cuda.synchronize()
+        ms[mode] = (time.perf_counter() - t0) / reps * 1e3
+    best = min(ms, key=ms.get)
+    plan.refine_mode = best
+    return {"mode": best, "ms": ms}

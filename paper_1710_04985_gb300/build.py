@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 
 SOURCES = ["api.cu", "analysis.cu", "solve_self.cu", "solve_level.cu", "solve_mrhs.cu", "aux.cu",
            "solve_tiled.cu", "solve_chain.cu", "noalloc.cu", "permute.cu",
-           "solve_column.cu", "kahn.cu", "solve_blocked.cu", "solve_parts.cu"]
+           "solve_column.cu", "kahn.cu", "solve_blocked.cu", "solve_parts.cu", "refine.cu"]
 CUSPARSE_SOURCES = ["cusparse_ref.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -183,6 +183,12 @@ struct sptrsv_plan_s {
     float* d32 = nullptr;
     size_t rd_elems = 0;
     unsigned long long* stats = nullptr;  // [0] max|r| [1] |A|_inf [2] max|x| [3] max|b|
+    // one-pass refinement (refine.cu): step buffers and per-step norms
+    void* rf_dpub = nullptr;
+    void* rf_xpub = nullptr;
+    size_t rf_bytes = 0;
+    unsigned long long* rf_norms = nullptr;  // [0, S) max|r^m|, [S, 2S) max|x^m|
+    double anorm = -1.0;                     // ||A||_inf of the current values (-1: unknown)
     int lanes = 4, block = 256, max_blocks = 0;
     // per-algorithm single-RHS shapes (lanes 0: use the plan's shape)
     int alg_lanes[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -196,6 +202,7 @@ struct sptrsv_plan_s {
     int part_rows = 0;   // partitioned solve: rows per part (0: automatic)
     int part_cluster = 1;  // partitioned solve: blocks per thread-block cluster
     sptrsv_algo_t default_algo = SPTRSV_ALGO_SELF;  // SPTRSV_ALGO_AUTO and refined solves
+    sptrsv_refine_t refine_mode = SPTRSV_REFINE_STAGED;
     int smem_optin = 0;  // shared memory a block may opt in to
     SpinPolicy spin{1ll << 24, 256, 128};
     int withhold = -1;
@@ -242,6 +249,9 @@ void destroy(sptrsv_plan_t P) {
     cudaFree(P->r32);
     cudaFree(P->d32);
     cudaFree(P->stats);
+    cudaFree(P->rf_dpub);
+    cudaFree(P->rf_xpub);
+    cudaFree(P->rf_norms);
     for (cudaEvent_t e : P->ev) cudaEventDestroy(e);
     delete P;
 }
@@ -1431,6 +1441,7 @@ sptrsv_status_t sptrsv_refresh_values(sptrsv_plan_t plan, void* stream) {
         CK(launch_to_f32(plan->nnz, 1, (const double*)plan->vals, 1, plan->vals32, nullptr,
                          plan->num_sms * 16, (cudaStream_t)stream));
     CK(refresh_permuted(plan, (cudaStream_t)stream));
+    plan->anorm = -1.0;  // the refined solve measures ||A||_inf again
     return SPTRSV_OK;
 }
 
@@ -1438,6 +1449,112 @@ sptrsv_status_t sptrsv_set_values(sptrsv_plan_t plan, const void* d_vals, void* 
     if (!plan || (plan->nnz > 0 && !d_vals)) return SPTRSV_ERR_INVALID_ARG;
     plan->vals = d_vals;
     return sptrsv_refresh_values(plan, stream);
+}
+
+// Refinement of one right-hand side in passes of the one-pass kernel
+// (refine.cu): the first pass solves from x = 0 and applies K corrections in
+// the same sweep; the host then reads the residual norm of every step and,
+// if none met `tol` and corrections remain, runs another pass from the
+// current x.  Needs the level-ordered copy and its FP32 values.
+sptrsv_status_t refine_in_passes(sptrsv_plan_t P, const double* d_b, double* d_x, long long ld,
+                                 int max_iter, double tol, int* iters, double* rel_resid,
+                                 cudaStream_t s) {
+    const int n = P->n;
+    const int grid16 = P->num_sms * 16;
+    ST(build_permuted(P, false, s));
+    ST(build_copy_f32(P, false, false, s));
+    const Levels& L = P->fwd;
+    const int S = kRefineMaxSteps + 1;
+    const size_t want = (size_t)S * n;
+    if (!P->rf_dpub || P->rf_bytes < want) {
+        CK(cudaStreamSynchronize(s));
+        cudaFree(P->rf_dpub);
+        cudaFree(P->rf_xpub);
+        P->rf_dpub = P->rf_xpub = nullptr;
+        P->rf_bytes = 0;
+        CK(cudaMalloc(&P->rf_dpub, sizeof(float) * want));
+        CK(cudaMalloc(&P->rf_xpub, sizeof(double) * want));
+        P->rf_bytes = want;
+    }
+    if (!P->rf_norms) CK(cudaMalloc(&P->rf_norms, 2 * S * sizeof(unsigned long long)));
+    if (!P->stats) CK(cudaMalloc(&P->stats, 4 * sizeof(unsigned long long)));
+    int launches = 0;
+    if (P->anorm < 0.0) {  // ||A||_inf of the current values, once
+        CK(cudaMemsetAsync(P->stats, 0, 4 * sizeof(unsigned long long), s));
+        CK(launch_residual(P->lanes, n, P->rowptr, P->colidx, (const double*)P->vals, P->unit, 1,
+                           d_b, ld, d_b, ld, nullptr, 0, nullptr, P->stats, true, grid16, s));
+        launches += 1;
+        unsigned long long h = 0;
+        CK(cudaMemcpyAsync(&h, P->stats + 1, sizeof(h), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        memcpy(&P->anorm, &h, sizeof(double));
+    }
+    // launch shape: the level-ordered form's (its tuned width), blocks of at most 512
+    const int a = (int)SPTRSV_ALGO_SELF_PERMUTED;
+    const int lanes = P->alg_lanes[a] > 0 ? P->alg_lanes[a] : P->lanes;
+    int block = P->alg_lanes[a] > 0 ? P->alg_block[a] : P->block;
+    if (block > 512) block = 512;
+    const int max_blocks = P->alg_lanes[a] > 0 ? P->alg_max_blocks[a] : P->max_blocks;
+    const int R = 32 / lanes;
+    const long long want_blocks = (((long long)n + R - 1) / R + block / 32 - 1) / (block / 32);
+    long long grid = (long long)refine_blocks_per_sm(lanes, block) * P->num_sms;
+    if (max_blocks > 0 && grid > max_blocks) grid = max_blocks;
+    if (grid > want_blocks) grid = want_blocks;
+    if (grid < 1) grid = 1;
+    RefineParams r;
+    memset(&r, 0, sizeof(r));
+    r.n = n;
+    r.ptr = L.pptr;
+    r.idx = L.pidx;
+    r.v64 = (const double*)L.pvals;
+    r.v32 = (const float*)L.pvals32;
+    r.jlev = L.jlev;
+    r.unit = P->unit;
+    r.diag_first = P->upper;
+    r.b = d_b;
+    r.ldb = ld;
+    r.x = d_x;
+    r.ldx = ld;
+    r.dpub = (float*)P->rf_dpub;
+    r.xpub = (double*)P->rf_xpub;
+    r.ticket = P->counters;
+    r.status = P->status;
+    r.rmax = P->rf_norms;
+    r.xmax = P->rf_norms + S;
+    r.spin = P->spin;
+    int applied = 0;
+    double rel = 0.0, bmax = 0.0;
+    for (bool first = true;; first = false) {
+        // a first pass takes three corrections: FP32 solves of a well-
+        // conditioned system reach FP64 accuracy after two, and the residual
+        // a pass measures last is that of its next-to-last iterate; later
+        // passes take the rest, at most kRefineMaxSteps steps each
+        const int left = max_iter - applied;
+        r.has_init = first ? 0 : 1;
+        r.K = first ? (left < 3 ? left : 3)
+                    : (left - 1 < kRefineMaxSteps ? left - 1 : kRefineMaxSteps);
+        CK(cudaMemsetAsync(P->rf_norms, 0, 2 * S * sizeof(unsigned long long), s));
+        CK(launch_refine_pass(lanes, r, (int)grid, block, s));
+        launches += 2;
+        unsigned long long h[2 * (kRefineMaxSteps + 1)];
+        CK(cudaMemcpyAsync(h, P->rf_norms, sizeof(h), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        double nr[2 * (kRefineMaxSteps + 1)];
+        memcpy(nr, h, sizeof(nr));
+        if (first) bmax = nr[0];  // step 0 of the first pass: r^0 = b
+        applied += first ? r.K : r.K + 1;
+        bool met = false;
+        for (int m = first ? 1 : 0; m <= r.K; ++m) {
+            const double denom = bmax + P->anorm * nr[S + m];
+            rel = denom > 0.0 ? nr[m] / denom : (nr[m] > 0.0 ? INFINITY : 0.0);
+            met = met || rel <= tol;
+        }
+        if (met || applied >= max_iter) break;
+    }
+    if (iters) *iters = applied;
+    if (rel_resid) *rel_resid = rel;
+    P->last_launches = launches;
+    return SPTRSV_OK;
 }
 
 sptrsv_status_t sptrsv_solve_refined(sptrsv_plan_t plan, const double* d_b, double* d_x,
@@ -1473,6 +1590,9 @@ sptrsv_status_t sptrsv_solve_refined(sptrsv_plan_t plan, const double* d_b, doub
     }
     if (!P->stats) CK(cudaMalloc(&P->stats, 4 * sizeof(unsigned long long)));
     CK(cudaMemsetAsync(P->stats, 0, 4 * sizeof(unsigned long long), s));
+    // One right-hand side in the one-pass form: every step in one sweep.
+    if (nrhs == 1 && max_iter >= 1 && P->refine_mode == SPTRSV_REFINE_ONE_PASS)
+        return refine_in_passes(P, d_b, d_x, ld, max_iter, tol, iters, rel_resid, s);
     // The FP32 solves run the plan's default form (sptrsv_set_default_algo,
     // e.g. the autotuner's choice) with that form's launch shape.  The forms
     // that can accumulate add each published correction straight into the
@@ -1521,6 +1641,19 @@ sptrsv_status_t sptrsv_solve_refined(sptrsv_plan_t plan, const double* d_b, doub
     if (iters) *iters = it;
     if (rel_resid) *rel_resid = rel;
     P->last_launches = launches;
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t sptrsv_set_refine_mode(sptrsv_plan_t plan, sptrsv_refine_t mode) {
+    if (!plan || (mode != SPTRSV_REFINE_STAGED && mode != SPTRSV_REFINE_ONE_PASS))
+        return SPTRSV_ERR_INVALID_ARG;
+    plan->refine_mode = mode;
+    return SPTRSV_OK;
+}
+
+sptrsv_status_t sptrsv_get_refine_mode(sptrsv_plan_t plan, int* mode) {
+    if (!plan || !mode) return SPTRSV_ERR_INVALID_ARG;
+    *mode = (int)plan->refine_mode;
     return SPTRSV_OK;
 }
 

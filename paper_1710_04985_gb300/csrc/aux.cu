@@ -110,12 +110,17 @@ __global__ void residual_k(int n, const int* __restrict__ ptr, const int* __rest
                 double s = 0.0, a_abs = 0.0;
                 for (int q = beg + sl; q < end; q += W) {
                     const int j = idx[q];
-                    const double a = (unit && j == i) ? 1.0 : vals[q];
+                    if (unit && j == i) continue;  // a unit diagonal is added below
+                    const double a = vals[q];
                     s += a * x[(long long)j * ldx + c];
                     if (c == 0) a_abs += fabs(a);
                 }
                 s = group_sum<W>(s, gmask);
                 if (c == 0 && want_norm) a_abs = group_sum<W>(a_abs, gmask);
+                if (unit) {  // the diagonal is 1, stored or not
+                    s += x[i * ldx + c];
+                    a_abs += 1.0;
+                }
                 if (sl == 0) {
                     const double rr = b[i * ldb + c] - s;
                     if (r) r[i * ldr + c] = rr;

@@ -231,6 +231,36 @@ cudaError_t launch_kahn_persistent(const int* dptr, const int* didx, int* count,
                                    unsigned long long* status, long long limit, int grid,
                                    int block, cudaStream_t s);
 
+// ---- refinement in one pass (refine.cu): on the level-ordered copy, K + 1
+// steps m = 0..K per row (residual in FP64, correction in FP32, update in
+// FP64), published per step in position order.
+constexpr int kRefineMaxSteps = 4;  // K <= kRefineMaxSteps per pass
+struct RefineParams {
+    int n;
+    const int* ptr;        // level-ordered copy: position k holds row jlev[k]
+    const int* idx;        // columns renumbered to positions
+    const double* v64;     // FP64 values of the copy (pre-scaled by 1/d(i) unless unit)
+    const float* v32;      // FP32 values of the copy (pre-scaled likewise)
+    const int* jlev;
+    int unit, diag_first;
+    const double* b;
+    long long ldb;
+    double* x;             // in: initial guess (has_init); out: x^{K+1}
+    long long ldx;
+    int has_init;
+    int K;
+    float* dpub;           // [K+1][n] corrections d^m, position order
+    double* xpub;          // [K+1][n] iterates x^m, position order
+    int* ticket;
+    unsigned long long* status;
+    unsigned long long* rmax;  // [K+1] max |r^m| (bits of a non-negative double)
+    unsigned long long* xmax;  // [K+1] max |x^m|
+    SpinPolicy spin;
+};
+cudaError_t launch_refine_pass(int lanes, const RefineParams& r, int grid, int block,
+                               cudaStream_t s);
+int refine_blocks_per_sm(int lanes, int block);
+
 // ---- auxiliary kernels (aux.cu)
 cudaError_t launch_grad_vals(bool f64, int lanes, int n, const int* ptr, const int* idx, bool unit,
                              const void* y, long long ldy, const void* x, long long ldx, int k,

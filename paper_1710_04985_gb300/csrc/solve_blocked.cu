@@ -16,9 +16,9 @@
 //  * hands its warps groups of 32/W consecutive positions from a
 //    shared-memory counter, so a slow group holds back only the rows that
 //    really depend on it;
-//  * prefetches the tile's rows into L2 as soon as it takes the tile: the
-//    tile a block takes next lies far ahead of the dependency frontier, so
-//    its loads become L2 hits by the time the frontier arrives.
+//  * prefetches the tile's rows into L2 in a window two rounds of groups
+//    ahead of the groups being taken, so their loads are L2 hits when the
+//    groups start.
 // A block starts its next tile only when every group of the current one is
 // done (one block barrier per tile); that tile is not yet on the critical
 // path when this happens.  Deadlock freedom: a group waits only on earlier
@@ -159,8 +159,15 @@ __global__ void __launch_bounds__(1024) blocked_solve_k1(SolveParams p, int tile
         if (CS == 1)
             for (int k = threadIdx.x; k < in_tile; k += blockDim.x)
                 xs[k] = Marker<T>::pending_value();
-        if (in_tile > 0) {  // the tile's rows are contiguous in the copy: one L2 prefetch per 128 B line
-            const long long q0 = p.ptr[p0], q1 = p.ptr[p0 + in_tile];
+        // L2 prefetch of the tile's rows (contiguous in the copy), one 128-byte
+        // line per request, in a window that stays two rounds of groups ahead
+        // of the groups being taken: the first rows now, the rest as groups are
+        // taken.  Prefetching the whole tile at once made concurrent tiles
+        // evict each other's lines (and the published values) from L2.
+        const int pf_rows = (int)(blockDim.x >> 5) * R * 2;
+        if (in_tile > 0) {
+            const int m = in_tile < pf_rows ? in_tile : pf_rows;
+            const long long q0 = p.ptr[p0], q1 = p.ptr[p0 + m];
             for (long long q = q0 + 32ll * threadIdx.x; q < q1; q += 32ll * blockDim.x)
                 prefetch_l2(p.idx + q);
             for (long long q = q0 + (128 / sizeof(T)) * threadIdx.x; q < q1;
@@ -174,6 +181,18 @@ __global__ void __launch_bounds__(1024) blocked_solve_k1(SolveParams p, int tile
             if (lane == 0) g = atomicAdd(&s_next, 1);
             g = __shfl_sync(FULL, g, 0);
             if (g >= groups) break;
+            {   // keep the prefetch window: the rows pf_rows positions ahead
+                const int a0 = g * R + pf_rows;
+                if (a0 < in_tile) {
+                    const int a1 = a0 + R < in_tile ? a0 + R : in_tile;
+                    const long long q0 = p.ptr[p0 + a0], q1 = p.ptr[p0 + a1];
+                    for (long long q = q0 + 32ll * lane; q < q1; q += 32ll * 32)
+                        prefetch_l2(p.idx + q);
+                    for (long long q = q0 + (128 / sizeof(T)) * lane; q < q1;
+                         q += (long long)(128 / sizeof(T)) * 32)
+                        prefetch_l2(vals + q);
+                }
+            }
             const int off = g * R + grp;  // this lane group's position in the tile
             const long long k = p0 + off;
             const bool has_row = off < in_tile;

@@ -27,11 +27,14 @@
 // cut into ceil(len/S) pieces of balanced length; shorter blocks that start
 // in the same window of S/2 positions share one part (so a part never holds
 // more than S rows).  A part never straddles two blocks unless all of them
-// fit in it whole.  The parts are then handed out deepest block first (the
-// block's level count), ties in order of substitution: the pieces of one
-// block keep their order, so every part still depends only on parts handed
-// out before it, while the longest dependency chains of a batch start first
-// instead of waiting behind short systems.
+// fit in it whole.  The parts are then handed out by piece index first
+// (every block's first piece, then every second piece, ...), deepest block
+// (its level count) first among equal pieces, then in order of substitution:
+// the pieces of one block keep their order, so every part still depends only
+// on parts handed out before it; the longest dependency chains of a batch
+// start first instead of waiting behind short systems, and a block's later
+// pieces, which would mostly wait for its earlier ones, are taken only after
+// every system has started.
 #include "internal.h"
 
 namespace sptrsv {

@@ -223,6 +223,23 @@ class TriangularPlan:
                                                _stream_handle(stream)), "sptrsv_solve_refined")
         return out, it.value, rel.value
 
+    REFINE_MODES = {"staged": _lib.REFINE_STAGED, "one_pass": _lib.REFINE_ONE_PASS}
+
+    @property
+    def refine_mode(self):
+        """How ``solve_refined`` refines one right-hand side: "staged" (an
+        FP32 solve pass and an FP64 residual pass per step) or "one_pass"
+        (every step in one self-scheduled sweep)."""
+        m = ctypes.c_int()
+        check(_lib.load().sptrsv_get_refine_mode(self._h, ctypes.byref(m)),
+              "sptrsv_get_refine_mode")
+        return {v: k for k, v in self.REFINE_MODES.items()}[m.value]
+
+    @refine_mode.setter
+    def refine_mode(self, name):
+        check(_lib.load().sptrsv_set_refine_mode(self._h, self.REFINE_MODES[name]),
+              "sptrsv_set_refine_mode")
+
     def set_values(self, vals, stream=None):
         if vals.dtype != self.dtype or vals.numel() != self.nnz or not vals.is_contiguous():
             raise ValueError("set_values: same dtype and length, contiguous")

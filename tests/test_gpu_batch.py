@@ -4,8 +4,8 @@ CPU oracle, through the C ABI).
 A block-diagonal batch decouples at every system boundary: no row of a later
 system depends on a row of an earlier one.  The partitioned solve finds
 these boundaries itself, cuts long systems into balanced parts, packs short
-neighbouring systems into one part and hands the parts out deepest system
-first.  The tests check that layout against the systems the batch was built
+neighbouring systems into one part and hands out every system's first part
+(deepest system first) before any second part.  The tests check that layout against the systems the batch was built
 from, and every solution against the oracle's solve of each system alone.
 """
 import numpy as np

@@ -613,11 +613,14 @@ def test_grad_vals_matches_oracle(name):
             assert relerr(g, ref) <= 1e-14
 
 
-def test_residual_matches_oracle():
-    A = mat("general")
+@pytest.mark.parametrize("name", ["general", "ilu_L", "unit_nodiag", "general_upper"])
+def test_residual_matches_oracle(name):
+    """r = b - A x in FP64; a unit diagonal counts as 1 whether it is stored
+    (ILU L factor) or not."""
+    A = mat(name)
     b = synth.uniform((A.n, 2), 22)
     x = synth.uniform((A.n, 2), 23)
-    ref = oracle.residual(A.rowptr, A.colidx, A.vals, b, x)
+    ref = oracle.residual(A.rowptr, A.colidx, A.vals, b, x, unit=A.unit)
     with plan_for(A) as p:
         r = p.residual(torch.tensor(b, device=dev()), torch.tensor(x, device=dev()))
         assert relerr(r, ref) <= 1e-14
@@ -703,6 +706,41 @@ def test_fp32_with_fp64_refinement(name, k, algo):
                                 unit=A.unit)
             x2, _, _ = p.solve_refined(torch.tensor(b, device=dev()))
             assert relerr(x2, ref2) <= TOL64
+
+
+@pytest.mark.parametrize("name", ["general", "ilu_L", "ilu_U", "long_rows", "general_upper",
+                                  "unit_nodiag"])
+def test_one_pass_refinement_steps_and_passes(name):
+    """One right-hand side in the one-pass form: every refinement step runs in
+    one self-scheduled sweep.  Its result meets the FP64 oracle like the
+    staged form's; with tol = 0 the solve keeps going pass after pass (later
+    passes start from the current x) until max_iter corrections are spent;
+    max_iter = 1 stops after the first pass's single correction."""
+    A = mat(name)
+    b = synth.uniform(A.n, 71)
+    ref = oracle.solve(A.rowptr, A.colidx, A.vals, b, upper=A.upper, unit=A.unit)
+    with plan_for(A) as p:
+        assert p.refine_mode == "staged"            # the default
+        p.refine_mode = "one_pass"
+        assert p.refine_mode == "one_pass"
+        bt = torch.tensor(b, device=dev())
+        for lanes in (1, 4, 32):
+            p.set_tuning(lanes, 256, 0)
+            x, iters, rel = p.solve_refined(bt)
+            assert relerr(x, ref) <= TOL64, (lanes, iters, rel)
+            assert 1 <= iters <= 10 and rel <= 8 * 2.0 ** -52
+        x, iters, rel = p.solve_refined(bt, max_iter=7, tol=0.0)
+        assert iters == 7 and relerr(x, ref) <= TOL64
+        x, iters, rel = p.solve_refined(bt, max_iter=1)
+        assert iters == 1 and relerr(x, ref) <= 1e-9
+        p.refine_mode = "staged"
+        xs, its, rels = p.solve_refined(bt)
+        assert relerr(xs, ref) <= TOL64
+        from paper_1710_04985_gb300 import autotune
+        res = autotune.tune_refine(p, bt)
+        assert p.refine_mode == res["mode"] and set(res["ms"]) == {"staged", "one_pass"}
+        assert relerr(p.solve_refined(bt)[0], ref) <= TOL64
+        assert p.status() == (0, -1)
 
 
 # ---------------------------------------------------------------- batching
