@@ -434,24 +434,6 @@ SPTRSV_API sptrsv_status_t sptrsv_set_tiling(sptrsv_plan_t plan, int tile_rows,
 SPTRSV_API sptrsv_status_t sptrsv_set_partition(sptrsv_plan_t plan, int part_rows,
                                                 int cluster_blocks);
 
-/* Level bands of SPTRSV_ALGO_SELF_PARTITIONED (0, the default: none).  With
- * band_levels = B > 0 the parts of sptrsv_set_partition become ranges, and a
- * part is the set of rows of one range whose level (Sec. 4.1) lies in one
- * band [kB, (k+1)B); parts are handed out band by band, ranges in their
- * hand-out order inside a band, each by level inside.  Every dependency of a
- * row then lies in its own part at a lower level or in a part handed out
- * earlier.  Only where a dependency crosses a range boundary or a band
- * boundary does it wait on L2; on a 3-D grid in natural order a range of
- * several grid planes and a band of tens of levels make most hops of the
- * critical path shared-memory hops.  The range size (part_rows) is then not
- * held to the shared-memory limit; a (range, band) pair longer than that
- * limit is cut into balanced pieces in its level order.  B * number of ranges
- * must stay below 2^30 (SPTRSV_ERR_INVALID_ARG at the next partitioned solve
- * otherwise).  The copy is rebuilt on the next partitioned solve when B
- * changes.  band_levels < 0: SPTRSV_ERR_INVALID_ARG. */
-SPTRSV_API sptrsv_status_t sptrsv_set_partition_bands(sptrsv_plan_t plan, int band_levels);
-SPTRSV_API sptrsv_status_t sptrsv_get_partition_bands(sptrsv_plan_t plan, int *band_levels);
-
 /* The part size the next partitioned solve uses (after the automatic choice
  * and the shared-memory limit) and its cluster size (1: no clusters). */
 SPTRSV_API sptrsv_status_t sptrsv_get_partition(sptrsv_plan_t plan, int *part_rows,

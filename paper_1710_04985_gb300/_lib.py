@@ -60,8 +60,6 @@ SIGNATURES = [
     ("sptrsv_set_tiling", _c_int, [_vp, _c_int, _c_int]),
     ("sptrsv_set_partition", _c_int, [_vp, _c_int, _c_int]),
     ("sptrsv_get_partition", _c_int, [_vp, _ip, _ip]),
-    ("sptrsv_set_partition_bands", _c_int, [_vp, _c_int]),
-    ("sptrsv_get_partition_bands", _c_int, [_vp, _ip]),
     ("sptrsv_partition_info", _c_int, [_vp, _c_int, _ip, _ip, _ip, _pp, _pp]),
     ("sptrsv_levels", _c_int, [_vp, _c_int, _ip, _pp, _pp, _pp]),
     ("sptrsv_transpose_pattern", _c_int, [_vp, _pp, _pp, _pp]),

@@ -65,8 +65,7 @@ struct Levels {
     // qpart: first position of each part (qnparts + 1 entries, parts in the
     // order they are handed out), qmaxpart the longest part, qnblocks the
     // independent blocks the substitution order splits into.
-    // qB: levels per band of that copy (0: parts are the ranges themselves).
-    int qS = 0, qB = 0;
+    int qS = 0;
     int* qord = nullptr;
     int* qipos = nullptr;
     int* qptr = nullptr;
@@ -100,7 +99,7 @@ void free_parts(Levels& L) {
     cudaFree(L.xq32);
     L.qord = L.qipos = L.qptr = L.qidx = L.qpart = nullptr;
     L.qvals = L.xq = L.qvals32 = L.xq32 = nullptr;
-    L.qS = L.qB = L.qnparts = L.qmaxpart = L.qnblocks = 0;
+    L.qS = L.qnparts = L.qmaxpart = L.qnblocks = 0;
 }
 
 struct DeviceGuard {
@@ -202,7 +201,6 @@ struct sptrsv_plan_s {
     bool tile_level_order = false;
     int part_rows = 0;   // partitioned solve: rows per part (0: automatic)
     int part_cluster = 1;  // partitioned solve: blocks per thread-block cluster
-    int part_band = 0;     // partitioned solve: levels per band (0: no bands)
     sptrsv_algo_t default_algo = SPTRSV_ALGO_SELF;  // SPTRSV_ALGO_AUTO and refined solves
     sptrsv_refine_t refine_mode = SPTRSV_REFINE_STAGED;
     int smem_optin = 0;  // shared memory a block may opt in to
@@ -732,13 +730,11 @@ int max_part_rows(sptrsv_plan_t P) {
 }
 
 // The part size of the next partitioned solve: the plan's setting or the
-// rows divided evenly over the SMs, at most max_part_rows.  With level bands
-// this is the size of a range, which the bands cut into parts: only those
-// are held to max_part_rows.
+// rows divided evenly over the SMs, at most max_part_rows.
 int resolve_part_rows(sptrsv_plan_t P) {
     long long S = P->part_rows > 0 ? P->part_rows
                                    : ((long long)P->n + P->num_sms - 1) / P->num_sms;
-    const int cap = P->part_band > 0 ? (P->n > 0 ? P->n : 1) : max_part_rows(P);
+    const int cap = max_part_rows(P);
     if (S > cap) S = cap;
     if (S < 1) S = 1;
     return (int)S;
@@ -750,18 +746,12 @@ int resolve_part_rows(sptrsv_plan_t P) {
 // blocks, short blocks packed together) and their hand-out order (deepest
 // block first), the level order jlev stably re-sorted by part, its inverse,
 // the copy with columns renumbered to positions, its self-check (every entry
-// names its own or an earlier position) and the publication buffer.  With
-// level bands of B levels (sptrsv_set_partition_bands) those parts are
-// ranges: a part is then the rows of one range whose levels fall in one band
-// (level / B), parts are handed out band by band and by range rank inside a
-// band, and a pair longer than the shared-memory limit is cut into balanced
-// pieces in its level order (short neighbouring pairs share a part).
+// names its own or an earlier position) and the publication buffer.
 // Allocates and synchronises s.
 sptrsv_status_t build_parts(sptrsv_plan_t P, bool trans, cudaStream_t s) {
     Levels& L = trans ? P->trn : P->fwd;
     const int S = resolve_part_rows(P);
-    const int B = P->part_band;
-    if (L.qord && L.qS == S && L.qB == B) return SPTRSV_OK;
+    if (L.qord && L.qS == S) return SPTRSV_OK;
     if (capturing(s)) return SPTRSV_ERR_NOT_SUPPORTED;
     CK(cudaStreamSynchronize(s));
     free_parts(L);
@@ -785,9 +775,8 @@ sptrsv_status_t build_parts(sptrsv_plan_t P, bool trans, cudaStream_t s) {
     if (e == cudaSuccess) e = cudaMalloc(&xq, esize * N);
     // scratch (ints): diff n+1, cover n+2, bflag n, bscan n+1, bstart n+1,
     // depth n, pflag n, pscan n+1, pstart n+1, pkey n, horder n, prank n,
-    // psize n, rowkey n, lens n, 2 counters | radix sort: 4 n + 2 hist |
-    // bands: rflag n, rscan n+1, rstart n+1, bpflag n, bpscan n+1
-    const size_t scratch_ints = 27 * N + 24 + 2 * (size_t)hist_n;
+    // psize n, rowkey n, lens n, 2 counters | radix sort: 4 n + 2 hist
+    const size_t scratch_ints = 22 * N + 16 + 2 * (size_t)hist_n;
     if (e == cudaSuccess) e = cudaMalloc(&scratch, sizeof(int) * scratch_ints);
     int* diff = scratch;
     int* cover = diff + (N + 1);
@@ -814,12 +803,7 @@ sptrsv_status_t build_parts(sptrsv_plan_t P, bool trans, cudaStream_t s) {
     int* piece = hist_scan + hist_n;
     int* pkey2 = piece + N;
     int* horder1 = pkey2 + N;
-    int* rflag = horder1 + N;
-    int* rscan = rflag + N;
-    int* rstart = rscan + (N + 1);
-    int* bpflag = rstart + (N + 1);
-    int* bpscan = bpflag + N;
-    int nb = 0, np = 0, maxpart = 0, npb = 0;
+    int nb = 0, np = 0, maxpart = 0;
     // independent blocks: no dependency span covers their first position
     if (e == cudaSuccess) e = cudaMemsetAsync(diff, 0, sizeof(int) * (N + 1), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(depth, 0, sizeof(int) * N, s);
@@ -838,11 +822,7 @@ sptrsv_status_t build_parts(sptrsv_plan_t P, bool trans, cudaStream_t s) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(&np, pscan + n, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess && (np < 1 || np > n || nb < 1 || nb > n)) e = cudaErrorUnknown;
-    const long long nbands = B > 0 ? ((long long)(L.nlev > 0 ? L.nlev : 1) + B - 1) / B : 1;
-    // the pair keys must fit the sort's 31 bits: too many bands times ranges
-    const bool too_many = nbands * np > (1ll << 30);
-    if (too_many) e = cudaErrorUnknown;
-    if (e == cudaSuccess && B == 0) e = cudaMalloc(&qpart, sizeof(int) * ((size_t)np + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&qpart, sizeof(int) * ((size_t)np + 1));
     // hand-out order: by piece index inside the block (every first piece,
     // then every second piece, ...), deepest block first among equal pieces,
     // then order of substitution (SPTRSV_PART_ORDER=1: deepest block first,
@@ -863,40 +843,13 @@ sptrsv_status_t build_parts(sptrsv_plan_t P, bool trans, cudaStream_t s) {
                                   v_b, hist, hist_scan, P->status, s);
     }
     if (e == cudaSuccess) e = launch_inverse_perm(horder, np, prank, s);
-    if (B == 0) {
-        if (e == cudaSuccess) e = launch_part_sizes(np, horder, pstart, psize, counters, s);
-        if (e == cudaSuccess) e = launch_exclusive_scan(psize, qpart, np, s);
-        if (e == cudaSuccess) e = launch_row_part_keys(n, L.jlev, upper, pscan, prank, rowkey, s);
-        // the copy: rows by part (hand-out order), by level inside a part
-        if (e == cudaSuccess)
-            e = radix_sort_values(rowkey, L.jlev, n, bits_for(np - 1), qord, k_a, v_a, k_b, v_b,
-                                  hist, hist_scan, P->status, s);
-    } else {
-        // the copy: rows by (band, range rank), by level inside a pair
-        const int cap = max_part_rows(P);
-        if (e == cudaSuccess)
-            e = launch_row_band_keys(n, L.jlev, upper, L.lev, B, np, pscan, prank, rowkey, s);
-        if (e == cudaSuccess)
-            e = radix_sort_values(rowkey, L.jlev, n, bits_for((int)(nbands * np - 1)), qord, k_a,
-                                  v_a, k_b, v_b, hist, hist_scan, P->status, s);
-        // parts: runs of equal key in the copy, long runs cut into balanced
-        // pieces of at most `cap` rows, short neighbouring runs packed
-        if (e == cudaSuccess)
-            e = launch_row_band_keys(n, qord, upper, L.lev, B, np, pscan, prank, rowkey, s);
-        if (e == cudaSuccess) e = launch_key_flags(n, rowkey, rflag, s);
-        if (e == cudaSuccess) e = launch_exclusive_scan(rflag, rscan, n, s);
-        if (e == cudaSuccess) e = launch_flag_scatter(n, rflag, rscan, rstart, s);
-        if (e == cudaSuccess) e = launch_part_flags(n, cap, rscan, rstart, bpflag, s);
-        if (e == cudaSuccess) e = launch_exclusive_scan(bpflag, bpscan, n, s);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(&npb, bpscan + n, sizeof(int), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e == cudaSuccess && (npb < 1 || npb > n)) e = cudaErrorUnknown;
-        if (e == cudaSuccess) e = cudaMalloc(&qpart, sizeof(int) * ((size_t)npb + 1));
-        if (e == cudaSuccess) e = launch_flag_scatter(n, bpflag, bpscan, qpart, s);
-        if (e == cudaSuccess) e = launch_part_max(npb, qpart, counters, s);
-        np = npb;
-    }
+    if (e == cudaSuccess) e = launch_part_sizes(np, horder, pstart, psize, counters, s);
+    if (e == cudaSuccess) e = launch_exclusive_scan(psize, qpart, np, s);
+    if (e == cudaSuccess) e = launch_row_part_keys(n, L.jlev, upper, pscan, prank, rowkey, s);
+    // the copy: rows by part (hand-out order), by level inside a part
+    if (e == cudaSuccess)
+        e = radix_sort_values(rowkey, L.jlev, n, bits_for(np - 1), qord, k_a, v_a, k_b, v_b,
+                              hist, hist_scan, P->status, s);
     if (e == cudaSuccess) e = launch_inverse_perm(qord, n, qipos, s);
     if (e == cudaSuccess) e = launch_ordered_lengths(n, ptr, qord, lens, s);
     if (e == cudaSuccess) e = launch_exclusive_scan(lens, qptr, n, s);
@@ -908,12 +861,10 @@ sptrsv_status_t build_parts(sptrsv_plan_t P, bool trans, cudaStream_t s) {
                                               cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     sptrsv_status_t rc = e == cudaSuccess ? SPTRSV_OK
-                         : too_many ? SPTRSV_ERR_INVALID_ARG
                          : e == cudaErrorUnknown ? SPTRSV_ERR_INTERNAL : cuda_fail(e);
     int row = -1;
     if (rc == SPTRSV_OK && take_status(P, s, &row) != SPTRSV_OK) rc = SPTRSV_ERR_INTERNAL;
-    if (rc == SPTRSV_OK && (maxpart < 1 || maxpart > (B > 0 ? max_part_rows(P) : S)))
-        rc = SPTRSV_ERR_INTERNAL;
+    if (rc == SPTRSV_OK && (maxpart < 1 || maxpart > S)) rc = SPTRSV_ERR_INTERNAL;
     cudaFree(scratch);
     if (rc != SPTRSV_OK) {
         cudaFree(qord);
@@ -926,7 +877,6 @@ sptrsv_status_t build_parts(sptrsv_plan_t P, bool trans, cudaStream_t s) {
         return rc;
     }
     L.qS = S;
-    L.qB = B;
     L.qord = qord;
     L.qipos = qipos;
     L.qptr = qptr;
@@ -1793,18 +1743,6 @@ sptrsv_status_t sptrsv_set_partition(sptrsv_plan_t plan, int part_rows, int clus
         return SPTRSV_ERR_INVALID_ARG;
     plan->part_rows = part_rows;
     plan->part_cluster = c > 1 ? c : 1;
-    return SPTRSV_OK;
-}
-
-sptrsv_status_t sptrsv_set_partition_bands(sptrsv_plan_t plan, int band_levels) {
-    if (!plan || band_levels < 0) return SPTRSV_ERR_INVALID_ARG;
-    plan->part_band = band_levels;
-    return SPTRSV_OK;
-}
-
-sptrsv_status_t sptrsv_get_partition_bands(sptrsv_plan_t plan, int* band_levels) {
-    if (!plan || !band_levels) return SPTRSV_ERR_INVALID_ARG;
-    *band_levels = plan->part_band;
     return SPTRSV_OK;
 }
 

@@ -145,14 +145,6 @@ cudaError_t launch_part_sizes(int np, const int* horder, const int* pstart, int*
 // key[k] = prank[part of row jlev[k]].
 cudaError_t launch_row_part_keys(int n, const int* jlev, bool upper, const int* pscan,
                                  const int* prank, int* key, cudaStream_t s);
-// key[k] = (lev[rows[k]] / B) * np + prank[part of rows[k]] (level bands).
-cudaError_t launch_row_band_keys(int n, const int* rows, bool upper, const int* lev, int B,
-                                 int np, const int* pscan, const int* prank, int* key,
-                                 cudaStream_t s);
-// flag[k] = 1 where a run of equal keys starts (k = 0 always).
-cudaError_t launch_key_flags(int n, const int* key, int* flag, cudaStream_t s);
-// atomic max into *maxsize of the part lengths pstart[r+1] - pstart[r].
-cudaError_t launch_part_max(int np, const int* pstart, int* maxsize, cudaStream_t s);
 
 // ---- level-ordered copy (permute.cu)
 // lens[k] = length of row jlev[k].

@@ -175,41 +175,6 @@ __global__ void row_part_keys_k(int n, const int* __restrict__ jlev, int upper,
     }
 }
 
-// Level bands (sptrsv_set_partition_bands).  key[k] = band of row
-// rows[k] (its level / B) times np plus the hand-out rank of its range part:
-// parts become (band, range) pairs, handed out band by band.  A dependency
-// has a lower level (band not later) and lies in the same or an earlier
-// range (rank not later), so it keeps an earlier key or sits in the same
-// pair at a lower level.
-__global__ void row_band_keys_k(int n, const int* __restrict__ rows, int upper,
-                                const int* __restrict__ lev, int B, int np,
-                                const int* __restrict__ pscan, const int* __restrict__ prank,
-                                int* key) {
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
-         k += (long long)gridDim.x * blockDim.x) {
-        const int i = rows[k];
-        const long long t = upper ? n - 1 - i : i;
-        key[k] = (lev[i] / B) * np + prank[pscan[t + 1] - 1];
-    }
-}
-
-// flag[k] = 1 where a run of equal keys starts.
-__global__ void key_flags_k(int n, const int* __restrict__ key, int* flag) {
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
-         k += (long long)gridDim.x * blockDim.x)
-        flag[k] = (k == 0 || key[k] != key[k - 1]) ? 1 : 0;
-}
-
-// *maxsize = longest part of pstart[0..np].
-__global__ void part_max_k(int np, const int* __restrict__ pstart, int* maxsize) {
-    int m = 0;
-    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < np;
-         r += (long long)gridDim.x * blockDim.x)
-        m = max(m, pstart[r + 1] - pstart[r]);
-    m = __reduce_max_sync(0xffffffffu, m);
-    if ((threadIdx.x & 31) == 0) atomicMax(maxsize, m);
-}
-
 #define SPTRSV_LAUNCH(kernel, m, ...)                        \
     do {                                                     \
         kernel<<<grid_for(m), 256, 0, s>>>(__VA_ARGS__);     \
@@ -275,26 +240,6 @@ cudaError_t launch_row_part_keys(int n, const int* jlev, bool upper, const int* 
                                  const int* prank, int* key, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     SPTRSV_LAUNCH(row_part_keys_k, n, n, jlev, upper ? 1 : 0, pscan, prank, key);
-    return cudaSuccess;
-}
-
-cudaError_t launch_row_band_keys(int n, const int* rows, bool upper, const int* lev, int B,
-                                 int np, const int* pscan, const int* prank, int* key,
-                                 cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    SPTRSV_LAUNCH(row_band_keys_k, n, n, rows, upper ? 1 : 0, lev, B, np, pscan, prank, key);
-    return cudaSuccess;
-}
-
-cudaError_t launch_key_flags(int n, const int* key, int* flag, cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    SPTRSV_LAUNCH(key_flags_k, n, n, key, flag);
-    return cudaSuccess;
-}
-
-cudaError_t launch_part_max(int np, const int* pstart, int* maxsize, cudaStream_t s) {
-    if (np <= 0) return cudaSuccess;
-    SPTRSV_LAUNCH(part_max_k, np, np, pstart, maxsize);
     return cudaSuccess;
 }
 

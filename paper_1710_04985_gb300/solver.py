@@ -319,21 +319,6 @@ class TriangularPlan:
         check(_lib.load().sptrsv_set_partition(self._h, int(part_rows), int(cluster_blocks)),
               "sptrsv_set_partition")
 
-    def set_partition_bands(self, band_levels=0):
-        """Level bands of the partitioned solve: with band_levels = B > 0 a
-        part is the rows of one range (set_partition) whose levels lie in one
-        band of B levels; 0 switches bands off."""
-        check(_lib.load().sptrsv_set_partition_bands(self._h, int(band_levels)),
-              "sptrsv_set_partition_bands")
-
-    @property
-    def partition_bands(self):
-        """Levels per band of the partitioned solve (0: no bands)."""
-        v = ctypes.c_int()
-        check(_lib.load().sptrsv_get_partition_bands(self._h, ctypes.byref(v)),
-              "sptrsv_get_partition_bands")
-        return v.value
-
     @property
     def partition(self):
         """Rows per part the next partitioned solve uses."""

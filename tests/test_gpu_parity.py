@@ -513,55 +513,6 @@ def test_partitioned_part_sizes(name):
                 p.set_partition(*bad)
 
 
-@pytest.mark.parametrize("name", ["ilu_L", "ilu_U", "general", "general_upper", "bidiag",
-                                  "diag", "long_rows", "unit_nodiag", "lap3d_27pt",
-                                  "lap2d_9pt_upper"])
-def test_partitioned_level_bands(name):
-    """Parts cut by level bands: bitwise equal to the self-scheduled solve for
-    every range size, band width and cluster size, and the layout holds what
-    the bands promise, checked from the oracle's levels: positions follow
-    the bands, every dependency sits at an earlier position, and no part
-    exceeds the shared-memory limit."""
-    A = mat(name)
-    b = synth.uniform(A.n, 31)
-    ref = oracle.solve(A.rowptr, A.colidx, A.vals, b, upper=A.upper, unit=A.unit)
-    lev, nlev, _, _ = oracle_levels(A)
-    with plan_for(A) as p:
-        bt = torch.tensor(b, device=dev())
-        p.set_tuning(1, 256, 0)
-        first = p.solve(bt)
-        assert relerr(first, ref) <= TOL64
-        cap = None
-        for rows, band, cl in ((0, 1, 1), (0, 7, 2), (600, 3, 1), (3000, 16, 4),
-                               (A.n, 5, 1), (A.n, nlev + 3, 2), (1, 2, 1)):
-            p.set_partition(rows, cl)
-            p.set_partition_bands(band)
-            assert p.partition_bands == band
-            assert torch.equal(p.solve(bt, algo="partitioned"), first), (rows, band, cl)
-            info = p.partition_info()
-            order = info["order"].cpu().numpy()
-            ptr = info["part_ptr"].cpu().numpy()
-            assert sorted(order.tolist()) == list(range(A.n))
-            pos = np.empty(A.n, np.int64)
-            pos[order] = np.arange(A.n)
-            bands = lev[order] // band
-            assert np.all(np.diff(bands) >= 0)                 # band by band
-            rowof = np.repeat(np.arange(A.n), np.diff(A.rowptr))
-            dep = A.colidx != rowof
-            assert np.all(pos[A.colidx[dep]] < pos[rowof[dep]])  # dependencies come earlier
-            assert ptr[0] == 0 and ptr[-1] == A.n and np.all(np.diff(ptr) >= 1)
-            assert info["max_part_rows"] == np.diff(ptr).max()
-            if cap is None:
-                p.set_partition(1 << 30, 1)
-                p.set_partition_bands(0)
-                cap = p.partition                              # the shared-memory limit
-            assert info["max_part_rows"] <= cap
-        assert p.status() == (0, -1)
-        from paper_1710_04985_gb300 import SptrsvError
-        with pytest.raises(SptrsvError):
-            p.set_partition_bands(-1)
-
-
 def _bad(n, rows, cols, vals, upper=False, unit=False):
     rows = np.asarray(rows)
     rowptr = np.zeros(n + 1, dtype=np.int32)
