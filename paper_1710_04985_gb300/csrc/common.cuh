@@ -119,6 +119,29 @@ __device__ __forceinline__ T group_sum(T v, unsigned mask) {
     return v;
 }
 
+// group_sum over the first `span` lanes of every group, the others holding
+// +0.0 (warp-uniform span, 1 <= span <= W): a butterfly level whose partner
+// lanes are all zero would add +0.0 and is skipped.  The result in the
+// group's first lane equals group_sum's (x + 0.0 == x; only a -0.0 partial
+// sum may come out as -0.0 instead of +0.0).  Each level is a dependent FP64
+// add of 64 cycles on GB300, so short rows save one per halving of span.
+template <int W, typename T>
+__device__ __forceinline__ T group_sum_span(T v, unsigned mask, int span) {
+#pragma unroll
+    for (int off = W / 2; off > 0; off >>= 1)
+        if (off < span) v += __shfl_xor_sync(mask, v, off);
+    return v;
+}
+
+// Warp-uniform span of the rows a warp holds: the longest of its rows'
+// stored entries, at most W (a lane at or past it holds no entry of its row).
+template <int W>
+__device__ __forceinline__ int warp_span(bool has_row, int len) {
+    if (W == 1) return 1;
+    const int l = has_row ? (len < W ? len : W) : 0;
+    return (int)__reduce_max_sync(0xffffffffu, (unsigned)l);
+}
+
 template <int W>
 __device__ __forceinline__ int group_max(int v, unsigned mask) {
 #pragma unroll

@@ -212,6 +212,7 @@ __global__ void __launch_bounds__(1024) blocked_solve_k1(SolveParams p, int tile
                 }
             }
             if (W > 1 && !p.unit && !p.prescaled) dinv = __shfl_sync(FULL, dinv, grp * W);
+            const int span = warp_span<W>(has_row, end - beg);
             int q0 = beg + sl;
             // position of the dependency, its offset in the tile, or (remote)
             // its address in another block's shared memory
@@ -305,7 +306,7 @@ __global__ void __launch_bounds__(1024) blocked_solve_k1(SolveParams p, int tile
                 const unsigned done = __ballot_sync(FULL, lane_done);
                 const bool fresh = !published && (done & gmask) == gmask;
                 if (__any_sync(FULL, fresh)) {
-                    const T tot = group_sum<W>(sum, FULL);
+                    const T tot = group_sum_span<W>(sum, FULL, span);
                     if (fresh && sl == 0 && i != p.withhold) publish_row(tot);
                 }
                 published = published || fresh;

@@ -113,6 +113,7 @@ __global__ void __launch_bounds__(1024) self_solve_k1(SolveParams p) {
             }
         }
         if (W > 1 && !p.unit && !p.prescaled) dinv = __shfl_sync(FULL, dinv, grp * W);
+        const int span = warp_span<W>(has_row, end - beg);
         // ---- per-lane chunk state: entries q0 + e*W, e < E
         int q0 = beg + sl;
         int c[E];
@@ -180,7 +181,7 @@ __global__ void __launch_bounds__(1024) self_solve_k1(SolveParams p) {
             const unsigned done = __ballot_sync(FULL, lane_done);
             const bool fresh = !published && (done & gmask) == gmask;
             if (__any_sync(FULL, fresh)) {  // FP64 is scarce on GB300: reduce only then
-                const T tot = group_sum<W>(sum, FULL);
+                const T tot = group_sum_span<W>(sum, FULL, span);
                 if (fresh && sl == 0 && i != p.withhold) publish_row(tot);
             }
             published = published || fresh;
