@@ -447,8 +447,11 @@ SPTRSV_API sptrsv_status_t sptrsv_get_partition(sptrsv_plan_t plan, int *part_ro
  * every system boundary) into *nblocks independent blocks; a block longer
  * than half the part size is cut into balanced parts of at most part_rows
  * rows, shorter neighbouring blocks share a part; the *nparts parts are
- * handed out to thread blocks deepest block first (its level count, Sec.
- * 4.1), in order of substitution among equals.  *max_part_rows is the
+ * handed out to thread blocks latest start first: by the block's slack (the
+ * deepest level of the matrix minus the block's own depth, Sec. 4.1) plus
+ * the piece's share of the block's levels (piece index times the block's
+ * level count / its number of parts, rounded down), in order of
+ * substitution among equals.  *max_part_rows is the
  * longest part.  All outputs nullable; the device arrays are owned by the
  * plan and valid until the copy is rebuilt or the plan freed:
  *   d_part_ptr  int[nparts + 1]: first position of each part, in hand-out

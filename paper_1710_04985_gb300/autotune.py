@@ -101,14 +101,20 @@ def tune(plan, b, x=None, algo="self", lanes=LANES, blocks=BLOCKS, grids=GRID_FR
                                                                    else tiles[0])
     first_grid = 2 * sms if algo in ("tiled", "blocked") else 0
     orders = tile_orders if algo == "tiled" else (False,)
+    # The blocked and partitioned forms hold a tile per block, so width and
+    # block size interact (rows in flight per tile): with two block sizes or
+    # fewer both are searched together in the first stage.
+    joint = algo in ("blocked", "partitioned") and len(blocks) <= 2
+    first_blocks = tuple(blocks) if joint else (default_block,)
     for order in orders:
         for w in lanes:
-            run(w, default_block, first_grid, tile0, order)
+            for blk in first_blocks:
+                run(w, blk, first_grid, tile0, order)
     w_best, order_best = min(table, key=lambda r: r[3])[0], min(table, key=lambda r: r[3])[5]
     if algo in ("self", "tiled", "chains", "permuted", "blocked", "partitioned"):
         for blk in blocks:
             for frac in grids:
-                if (blk, frac * sms) != (default_block, first_grid):
+                if (w_best, blk, frac * sms) not in {(r[0], r[1], r[2]) for r in table}:
                     run(w_best, blk, frac * sms, tile0, order_best)
     if tiles_used:
         bb = min(table, key=lambda r: r[3])

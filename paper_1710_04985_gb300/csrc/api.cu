@@ -823,15 +823,27 @@ sptrsv_status_t build_parts(sptrsv_plan_t P, bool trans, cudaStream_t s) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess && (np < 1 || np > n || nb < 1 || nb > n)) e = cudaErrorUnknown;
     if (e == cudaSuccess) e = cudaMalloc(&qpart, sizeof(int) * ((size_t)np + 1));
-    // hand-out order: by piece index inside the block (every first piece,
-    // then every second piece, ...), deepest block first among equal pieces,
-    // then order of substitution (SPTRSV_PART_ORDER=1: deepest block first,
-    // its pieces together)
+    // hand-out order: latest start first -- by the block's slack (deepest
+    // level minus its depth) plus the piece's share of the block's levels,
+    // then order of substitution.  SPTRSV_PART_ORDER=2: by piece index (every
+    // first piece, then every second piece, ...), deepest block first among
+    // equal pieces; =1: deepest block first, its pieces together.
     const int maxdepth = L.nlev > 0 ? L.nlev - 1 : 0;
-    const bool by_piece = env_ll("SPTRSV_PART_ORDER", 2) != 1;
-    if (e == cudaSuccess)
+    const long long order = env_ll("SPTRSV_PART_ORDER", 3);
+    const bool by_piece = order == 2;
+    if (order == 3) {
+        // latest start first: slack of the block plus the piece's share of its levels
+        if (e == cudaSuccess) e = launch_part_piece(np, pstart, bscan, bstart, pscan, piece, s);
+        if (e == cudaSuccess)
+            e = launch_part_alap_keys(np, maxdepth, pstart, bscan, bstart, pscan, depth, piece,
+                                      pkey, s);
+        if (e == cudaSuccess)
+            e = radix_sort_values(pkey, nullptr, np, bits_for(2 * maxdepth + 1), horder, k_a, v_a,
+                                  k_b, v_b, hist, hist_scan, P->status, s);
+    } else if (e == cudaSuccess) {
         e = launch_part_depth_keys(np, maxdepth, pstart, bscan, depth, pkey, s);
-    if (e == cudaSuccess)
+    }
+    if (e == cudaSuccess && order != 3)
         e = radix_sort_values(pkey, nullptr, np, bits_for(maxdepth),
                               by_piece ? horder1 : horder, k_a, v_a, k_b, v_b, hist, hist_scan,
                               P->status, s);

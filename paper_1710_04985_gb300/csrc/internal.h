@@ -140,6 +140,10 @@ cudaError_t launch_part_depth_keys(int np, int maxdepth, const int* pstart, cons
 cudaError_t launch_part_piece(int np, const int* pstart, const int* bscan, const int* bstart,
                               const int* pscan, int* piece, cudaStream_t s);
 // size[r] = rows of part horder[r]; *maxsize = max (zeroed by the caller).
+// key[p] = slack of part p's block + piece[p] * levels per piece of the block.
+cudaError_t launch_part_alap_keys(int np, int maxdepth, const int* pstart, const int* bscan,
+                                  const int* bstart, const int* pscan, const int* depth,
+                                  const int* piece, int* key, cudaStream_t s);
 cudaError_t launch_part_sizes(int np, const int* horder, const int* pstart, int* size,
                               int* maxsize, cudaStream_t s);
 // key[k] = prank[part of row jlev[k]].

@@ -27,14 +27,18 @@
 // cut into ceil(len/S) pieces of balanced length; shorter blocks that start
 // in the same window of S/2 positions share one part (so a part never holds
 // more than S rows).  A part never straddles two blocks unless all of them
-// fit in it whole.  The parts are then handed out by piece index first
-// (every block's first piece, then every second piece, ...), deepest block
-// (its level count) first among equal pieces, then in order of substitution:
-// the pieces of one block keep their order, so every part still depends only
-// on parts handed out before it; the longest dependency chains of a batch
-// start first instead of waiting behind short systems, and a block's later
-// pieces, which would mostly wait for its earlier ones, are taken only after
-// every system has started.
+// fit in it whole.  The parts are then handed out latest start first: a
+// part's key is the level at which it must start at the latest for its
+// block to finish with the deepest one -- the block's slack (deepest level
+// of the matrix minus the block's own depth) plus the piece's share of the
+// block's levels (piece index times levels per piece) -- and parts with
+// equal keys go in order of substitution.  Keys do not decrease along a
+// block's pieces, so every part still depends only on parts handed out
+// before it.  The pieces of the deepest systems of a batch are taken as the
+// frontier reaches them, and short systems, which have slack, fill the
+// blocks in between; handing out every system's first piece before any
+// second piece (the previous order) left the deepest system's later pieces
+// queued behind hundreds of short systems (batch of 512: 5.06 -> 4.64 ms).
 #include "internal.h"
 
 namespace sptrsv {
@@ -148,6 +152,25 @@ __global__ void part_piece_k(int np, const int* __restrict__ pstart,
     }
 }
 
+// key[p] = the estimated latest level at which part p can start: its
+// block's slack (deepest level minus the block's depth) plus its piece's
+// share of the block's levels (piece index times levels per piece).  Keys do
+// not decrease along a block's pieces, so a stable sort keeps them in order.
+__global__ void part_alap_keys_k(int np, int maxdepth, const int* __restrict__ pstart,
+                                 const int* __restrict__ bscan, const int* __restrict__ bstart,
+                                 const int* __restrict__ pscan, const int* __restrict__ depth,
+                                 const int* __restrict__ piece, int* key) {
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < np;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int b = bscan[pstart[p] + 1] - 1;
+        const int d = depth[b];
+        const int first = pscan[bstart[b] + 1] - 1;  // the block's first part
+        const int cnt = pscan[bstart[b + 1]] - first;  // parts starting in the block
+        const long long share = cnt > 1 ? (long long)piece[p] * (d + 1) / cnt : 0;
+        key[p] = (maxdepth - d) + (int)share;
+    }
+}
+
 // size[r] = rows of the part handed out r-th; atomic max of the sizes.
 __global__ void part_sizes_k(int np, const int* __restrict__ horder,
                              const int* __restrict__ pstart, int* size, int* maxsize) {
@@ -226,6 +249,15 @@ cudaError_t launch_part_piece(int np, const int* pstart, const int* bscan, const
                               const int* pscan, int* piece, cudaStream_t s) {
     if (np <= 0) return cudaSuccess;
     SPTRSV_LAUNCH(part_piece_k, np, np, pstart, bscan, bstart, pscan, piece);
+    return cudaSuccess;
+}
+
+cudaError_t launch_part_alap_keys(int np, int maxdepth, const int* pstart, const int* bscan,
+                                  const int* bstart, const int* pscan, const int* depth,
+                                  const int* piece, int* key, cudaStream_t s) {
+    if (np <= 0) return cudaSuccess;
+    SPTRSV_LAUNCH(part_alap_keys_k, np, np, maxdepth, pstart, bscan, bstart, pscan, depth, piece,
+                  key);
     return cudaSuccess;
 }
 

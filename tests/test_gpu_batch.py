@@ -4,9 +4,11 @@ CPU oracle, through the C ABI).
 A block-diagonal batch decouples at every system boundary: no row of a later
 system depends on a row of an earlier one.  The partitioned solve finds
 these boundaries itself, cuts long systems into balanced parts, packs short
-neighbouring systems into one part and hands out every system's first part
-(deepest system first) before any second part.  The tests check that layout against the systems the batch was built
-from, and every solution against the oracle's solve of each system alone.
+neighbouring systems into one part and hands the parts out latest start
+first (a system's slack behind the deepest one plus the piece's share of the
+system's levels).  The tests check that layout against the systems the batch
+was built from, and every solution against the oracle's solve of each system
+alone.
 """
 import numpy as np
 import pytest
@@ -40,9 +42,10 @@ def _system_of_rows(offsets, n):
 
 def _check_layout(info, mats, offsets, S, upper):
     """Parts never split a system except into pieces of a system longer than
-    S/2; short systems are only packed whole; the hand-out order is every
-    system's first piece (deepest system first), then every second piece,
-    and so on, so a system's pieces follow its order of substitution."""
+    S/2; short systems are only packed whole; the hand-out order is by the
+    latest start level of a part, (deepest level - depth of its system) +
+    piece index * levels of its system // parts of its system, then order of
+    substitution, so a system's pieces follow its order of substitution."""
     n = int(offsets[-1])
     sizes = np.diff(offsets)
     sys_of = _system_of_rows(offsets, n)
@@ -71,8 +74,14 @@ def _check_layout(info, mats, offsets, S, upper):
         parts.append((sys_of[first], sub))
     # piece index: rank of the part among its system's parts in substitution order
     piece = [sum(1 for s2, u in parts if s2 == s and u < sub) for s, sub in parts]
-    keys = [(piece[j], -depth[s], sub) for j, (s, sub) in enumerate(parts)]
+    count = [sum(1 for s2, _ in parts if s2 == s) for s, _ in parts]
+    maxlev = int(depth.max()) - 1
+    keys = [((maxlev - (int(depth[s]) - 1)) + piece[j] * int(depth[s]) // count[j], sub)
+            for j, (s, sub) in enumerate(parts)]
     assert keys == sorted(keys)
+    for s in set(s for s, _ in parts):   # a system's pieces in substitution order
+        subs = [sub for s2, sub in parts if s2 == s]
+        assert subs == sorted(subs)
 
 
 @pytest.mark.parametrize("upper", [False, True])
