@@ -1438,7 +1438,7 @@ sptrsv_status_t sptrsv_residual(sptrsv_plan_t plan, const double* d_b, const dou
     if (plan->n == 0) return SPTRSV_OK;
     if (!d_b || !d_x || !d_r) return SPTRSV_ERR_INVALID_ARG;
     DeviceGuard g(plan->device);
-    CK(launch_residual(plan->lanes, plan->n, plan->rowptr, plan->colidx,
+    CK(launch_residual(plan->n, plan->nnz, plan->rowptr, plan->colidx,
                        (const double*)plan->vals, plan->unit, nrhs, d_b, ld, d_x, ld, d_r, ld,
                        nullptr, nullptr, false, plan->num_sms * 16, (cudaStream_t)stream));
     plan->last_launches = 1;
@@ -1493,7 +1493,7 @@ sptrsv_status_t refine_in_passes(sptrsv_plan_t P, const double* d_b, double* d_x
     int launches = 0;
     if (P->anorm < 0.0) {  // ||A||_inf of the current values, once
         CK(cudaMemsetAsync(P->stats, 0, 4 * sizeof(unsigned long long), s));
-        CK(launch_residual(P->lanes, n, P->rowptr, P->colidx, (const double*)P->vals, P->unit, 1,
+        CK(launch_residual(n, P->nnz, P->rowptr, P->colidx, (const double*)P->vals, P->unit, 1,
                            d_b, ld, d_b, ld, nullptr, 0, nullptr, P->stats, true, grid16, s));
         launches += 1;
         unsigned long long h = 0;
@@ -1634,16 +1634,20 @@ sptrsv_status_t sptrsv_solve_refined(sptrsv_plan_t plan, const double* d_b, doub
     double rel = 0.0;
     for (;;) {
         // r = b - A x in FP64, its FP32 copy (the next right-hand side),
-        // max|r|, max|x| and (first pass) ||A||_inf, in one pass
+        // max|r|, max|x| and, once per set of values, ||A||_inf, in one pass
+        const bool want_norm = P->anorm < 0.0;
         CK(cudaMemsetAsync(P->stats, 0, 3 * sizeof(unsigned long long), s));
-        CK(launch_residual(P->lanes, n, P->rowptr, P->colidx, (const double*)P->vals, P->unit,
-                           nrhs, d_b, ld, d_x, ld, nullptr, 0, P->r32, P->stats, true, grid, s));
+        CK(launch_residual(n, P->nnz, P->rowptr, P->colidx, (const double*)P->vals, P->unit,
+                           nrhs, d_b, ld, d_x, ld, nullptr, 0, P->r32, P->stats, want_norm, grid,
+                           s));
         launches += 1;
         unsigned long long h[4];
         CK(cudaMemcpyAsync(h, P->stats, sizeof(h), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         double st[4];
         memcpy(st, h, sizeof(st));
+        if (want_norm) P->anorm = st[1];  // kept until the values change
+        else st[1] = P->anorm;
         const double denom = st[3] + st[1] * st[2];
         rel = denom > 0.0 ? st[0] / denom : (st[0] > 0.0 ? INFINITY : 0.0);
         if (rel <= tol || it >= max_iter) break;

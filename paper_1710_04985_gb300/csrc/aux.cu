@@ -26,6 +26,35 @@ __device__ __forceinline__ void block_max_to(unsigned long long* where, double v
     }
 }
 
+// Block-wide max of the bits of non-negative doubles (NaN, whose bits are
+// larger than infinity's, wins), then one atomic per block: integer
+// operations only, no FP64 instruction.
+__device__ __forceinline__ void block_max_bits_to(unsigned long long* where,
+                                                  unsigned long long v) {
+    __shared__ unsigned long long wmax[32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, off);
+        v = o > v ? o : v;
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) wmax[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? wmax[lane] : 0ull;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, off);
+            v = o > v ? o : v;
+        }
+        if (lane == 0 && v) atomicMax(where, v);
+    }
+}
+
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+    return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+}
+
 // ------------------------------------------------------------ gradient
 // g[q] = - sum_c y[i][c] x[j][c] for stored entry q = (i, j); zero on the
 // diagonal of a unit-diagonal matrix (it is not a parameter).
@@ -87,6 +116,11 @@ cudaError_t launch_grad_vals(bool f64, int lanes, int n, const int* ptr, const i
 }
 
 // ------------------------------------------------------------ residual (FP64)
+// On GB300 an FP64 warp instruction holds its sub-partition's FP64 unit for
+// ~76 cycles whatever its active lanes, and this pass is bound by that unit:
+// the width W is chosen so that lanes stay busy (about four entries per lane,
+// residual_lanes), the maxima are integer maxima of the bits of |v|, and the
+// sum of |a_ij| is formed only when the norm is asked for.
 template <int W>
 __global__ void residual_k(int n, const int* __restrict__ ptr, const int* __restrict__ idx,
                            const double* __restrict__ vals, int unit, int k,
@@ -97,7 +131,7 @@ __global__ void residual_k(int n, const int* __restrict__ ptr, const int* __rest
     const int lane = threadIdx.x & 31;
     const int sl = lane % W;
     const unsigned gmask = group_mask<W>(lane);
-    double rmax = 0.0, amax = 0.0, xmax = 0.0;
+    unsigned long long rmax = 0, amax = 0, xmax = 0;  // bits of non-negative doubles
     // Every lane of a block runs the same number of iterations so that the
     // block-wide reduction below is reached by all of them.
     const long long first = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / W;
@@ -113,41 +147,55 @@ __global__ void residual_k(int n, const int* __restrict__ ptr, const int* __rest
                     if (unit && j == i) continue;  // a unit diagonal is added below
                     const double a = vals[q];
                     s += a * x[(long long)j * ldx + c];
-                    if (c == 0) a_abs += fabs(a);
+                    if (c == 0 && want_norm) a_abs += fabs(a);  // FP64 adds only when asked
                 }
                 s = group_sum<W>(s, gmask);
                 if (c == 0 && want_norm) a_abs = group_sum<W>(a_abs, gmask);
                 if (unit) {  // the diagonal is 1, stored or not
                     s += x[i * ldx + c];
-                    a_abs += 1.0;
+                    if (c == 0 && want_norm) a_abs += 1.0;
                 }
                 if (sl == 0) {
                     const double rr = b[i * ldb + c] - s;
                     if (r) r[i * ldr + c] = rr;
                     if (r32) r32[i * k + c] = (float)rr;
-                    rmax = fmax(rmax, fabs(rr));
-                    xmax = fmax(xmax, fabs(x[i * ldx + c]));
-                    if (c == 0) amax = fmax(amax, a_abs);
+                    const unsigned long long rb = abs_bits(rr), xb = abs_bits(x[i * ldx + c]);
+                    rmax = rb > rmax ? rb : rmax;
+                    xmax = xb > xmax ? xb : xmax;
+                    if (c == 0 && want_norm) {
+                        const unsigned long long ab = abs_bits(a_abs);
+                        amax = ab > amax ? ab : amax;
+                    }
                 }
             }
         }
     }
     if (stats) {
-        block_max_to(stats, rmax);
+        block_max_bits_to(stats, rmax);
         __syncthreads();
-        block_max_to(stats + 2, xmax);
+        block_max_bits_to(stats + 2, xmax);
         if (want_norm) {
             __syncthreads();
-            block_max_to(stats + 1, amax);
+            block_max_bits_to(stats + 1, amax);
         }
     }
 }
 
-cudaError_t launch_residual(int lanes, int n, const int* ptr, const int* idx, const double* vals,
-                            bool unit, int k, const double* b, long long ldb, const double* x,
-                            long long ldx, double* r, long long ldr, float* r32,
+// Width of the residual pass: about four stored entries per lane (a power of
+// two in 1..32), from the average row length.
+int residual_lanes(int n, long long nnz) {
+    const double per_row = n > 0 ? (double)nnz / n : 1.0;
+    int w = 1;
+    while (w < 32 && 4.0 * (2 * w) <= per_row) w *= 2;
+    return w;
+}
+
+cudaError_t launch_residual(int n, long long nnz, const int* ptr, const int* idx,
+                            const double* vals, bool unit, int k, const double* b, long long ldb,
+                            const double* x, long long ldx, double* r, long long ldr, float* r32,
                             unsigned long long* stats, bool want_norm, int grid, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
+    const int lanes = residual_lanes(n, nnz);
     long long want = ((long long)n * lanes + 255) / 256;
     int g = (int)(want < grid ? want : grid);
     if (g < 1) g = 1;

@@ -273,9 +273,9 @@ cudaError_t launch_grad_vals(bool f64, int lanes, int n, const int* ptr, const i
 // contiguous [n][k]); stats (nullable): atomicMax of max|r| into stats[0],
 // of max|x| into stats[2] and, if want_norm, of max_i sum_j |A_ij| into
 // stats[1].
-cudaError_t launch_residual(int lanes, int n, const int* ptr, const int* idx, const double* vals,
-                            bool unit, int k, const double* b, long long ldb, const double* x,
-                            long long ldx, double* r, long long ldr, float* r32,
+cudaError_t launch_residual(int n, long long nnz, const int* ptr, const int* idx,
+                            const double* vals, bool unit, int k, const double* b, long long ldb,
+                            const double* x, long long ldx, double* r, long long ldr, float* r32,
                             unsigned long long* stats, bool want_norm, int grid, cudaStream_t s);
 // x = d (first) or x += d, FP64 x [n][ldx], FP32 d contiguous [n][k];
 // atomicMax of max|x| into *xmax.
