@@ -55,6 +55,18 @@ __device__ __forceinline__ void accumulate_published(const SolveParams& p, long 
     *a = p.acc_first ? (double)v : *a + (double)v;
 }
 
+// The value accumulate_with() will add to, loaded when the row is taken (off
+// the dependency path) rather than after its publication, where the load
+// would hold up the warp's other rows.
+__device__ __forceinline__ double accumulate_base(const SolveParams& p, long long i, int c) {
+    return (p.xacc && !p.acc_first) ? p.xacc[i * p.ldacc + c] : 0.0;
+}
+template <typename T>
+__device__ __forceinline__ void accumulate_with(const SolveParams& p, long long i, int c, T v,
+                                                double base) {
+    p.xacc[i * p.ldacc + c] = p.acc_first ? (double)v : base + (double)v;
+}
+
 // Column structure of the column-wise solve (solve_column.cu): the CSR of
 // the transpose of the system matrix, so row i lists the unknowns that
 // depend on unknown i, plus the dependency counters.

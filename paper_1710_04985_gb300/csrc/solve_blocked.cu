@@ -198,6 +198,7 @@ __global__ void __launch_bounds__(1024) blocked_solve_k1(SolveParams p, int tile
             const bool has_row = off < in_tile;
             int i = 0, beg = 0, end = 0;
             T dinv = T(1), sum = T(0);
+            double xbase = 0.0;  // refinement: the solution the row's value is added to
             if (has_row) {
                 i = p.jlev[k];
                 beg = p.ptr[k];
@@ -209,6 +210,7 @@ __global__ void __launch_bounds__(1024) blocked_solve_k1(SolveParams p, int tile
                     }
                     sum = b[(long long)i * p.ldb];
                     if (!p.unit) sum *= dinv;
+                    xbase = accumulate_base(p, i, 0);
                 }
             }
             if (W > 1 && !p.unit && !p.prescaled) dinv = __shfl_sync(FULL, dinv, grp * W);
@@ -278,7 +280,7 @@ __global__ void __launch_bounds__(1024) blocked_solve_k1(SolveParams p, int tile
                     sts_volatile(xs + off, xi);
                 st_relaxed(xp + k, xi);
                 if (p.xacc)
-                    accumulate_published(p, i, 0, xi);
+                    accumulate_with(p, i, 0, xi, xbase);
                 else
                     x[(long long)i * p.ldx] = xi;
             };

@@ -91,6 +91,7 @@ __global__ void __launch_bounds__(1024) self_solve_k1(SolveParams p) {
         const bool has_row = k < p.n;
         int i = 0, beg = 0, end = 0;
         T dinv = T(1), sum = T(0);
+        double xbase = 0.0;  // refinement: the solution the row's value is added to
         // identity of the row inside the pattern: its own column index
         const int self_col = PERM ? (int)k : 0;
         if (has_row) {
@@ -110,6 +111,7 @@ __global__ void __launch_bounds__(1024) self_solve_k1(SolveParams p) {
                 }
                 sum = b[(long long)i * p.ldb];
                 if (!p.unit) sum *= dinv;
+                xbase = accumulate_base(p, i, 0);
             }
         }
         if (W > 1 && !p.unit && !p.prescaled) dinv = __shfl_sync(FULL, dinv, grp * W);
@@ -153,7 +155,7 @@ __global__ void __launch_bounds__(1024) self_solve_k1(SolveParams p) {
             const T val = publishable(tot);
             st_relaxed(xpub + (PERM ? k : (long long)i * p.ldx), val);
             if (p.xacc)
-                accumulate_published(p, i, 0, val);
+                accumulate_with(p, i, 0, val, xbase);
             else if (PERM)
                 x[(long long)i * p.ldx] = val;
         };
