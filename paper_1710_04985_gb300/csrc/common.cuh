@@ -91,15 +91,19 @@ constexpr int kChunk = 4;
 
 // sum - a[0] v[0] - a[1] v[1] - ... over the live entries of a chunk, one FMA
 // each in entry order.  The dead slots of a chunk (the diagonal, past the
-// row's end) lie after its last live entry, and the loop stops there: a
-// predicated-off FP64 instruction still sits on the dependency chain of
-// `sum` (on GB300 each skipped slot saved ~50 ns per dependency hop).
+// row's end) lie before its first live entry (the diagonal of an upper row)
+// or after its last one (the diagonal of a lower row, the row's end), and the
+// loop covers only the slots in between: a predicated-off FP64 instruction
+// still sits on the dependency chain of `sum` for a whole FP64 issue slot (on
+// GB300 each skipped slot saved ~50 ns per dependency hop).
 template <typename T, int E>
 __device__ __forceinline__ T fold_chunk(T sum, const T (&a)[E], const T (&v)[E], unsigned live) {
     const int hi = 32 - __clz(live);
+    const int lo = __ffs(live) - 1;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         if (e >= hi) break;
+        if (e < lo) continue;
         if (live & (1u << e)) sum = fma(-a[e], v[e], sum);
     }
     return sum;
