@@ -149,3 +149,38 @@ def test_bench_tuning_row_reports_parts_and_clusters():
         [4, 256, 0, 2048, True]
     assert bench._tuning_row({"algo": "permuted", "best": (2, 128, 608, 0.4, 2048, False)}) == \
         [2, 128, 608, None, None]
+
+
+class _InteractingPlan(_ModelPlan):
+    """A plan whose best width depends on the block size (as on the
+    512-system batch: 8 lanes win at 512 threads, 16 lanes at 1024 win
+    overall)."""
+
+    def model_ms(self, algo):
+        lanes, block, _ = self.shape
+        table = {(8, 512): 6.0, (16, 512): 6.4, (8, 1024): 5.4, (16, 1024): 4.7}
+        return table.get((lanes, block), 9.0)
+
+
+def test_autotuner_searches_width_and_block_together(monkeypatch):
+    """For the tiled forms with two block sizes or fewer the first stage runs
+    every width at every block size, so a width that only wins at the larger
+    block is found."""
+    import types
+
+    import torch
+
+    from paper_1710_04985_gb300 import autotune
+    monkeypatch.setattr(torch.cuda, "get_device_properties",
+                        lambda dev: types.SimpleNamespace(multi_processor_count=152))
+    monkeypatch.setattr(autotune, "time_solve",
+                        lambda plan, b, x, algo="self", reps=3, transpose=False:
+                        plan.model_ms(algo))
+    p = _InteractingPlan()
+    b = torch.zeros(1000, dtype=torch.float64)
+    res = autotune.tune(p, b, torch.empty_like(b), algo="partitioned", use_cache=False,
+                        **autotune.QUICK["partitioned"])
+    lanes, block = res["best"][:2]
+    assert (lanes, block) == (16, 1024) and abs(res["best"][3] - 4.7) < 1e-12
+    tried = {(r[0], r[1]) for r in res["table"]}
+    assert {(8, 512), (8, 1024), (16, 512), (16, 1024)} <= tried
