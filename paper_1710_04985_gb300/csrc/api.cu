@@ -637,7 +637,8 @@ sptrsv_status_t build_permuted(sptrsv_plan_t P, bool trans, cudaStream_t s) {
     if (e == cudaSuccess) e = launch_exclusive_scan(lens, pptr, n, s);
     if (e == cudaSuccess)
         e = launch_permute_rows(P->f64, n, ptr, idx, vmap, P->vals, L.jlev, L.ipos, pptr, pidx,
-                                pvals, P->num_sms * 16, s, copy_diag(P, trans));
+                                pvals, P->num_sms * 16, s, copy_diag(P, trans),
+                                trans ? !P->upper : P->upper);
     if (e == cudaSuccess) e = launch_verify_permuted(n, pptr, pidx, P->status, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     sptrsv_status_t rc = e == cudaSuccess ? SPTRSV_OK : cuda_fail(e);
@@ -692,7 +693,8 @@ cudaError_t refresh_permuted(sptrsv_plan_t P, cudaStream_t s) {
         cudaError_t e = launch_permute_rows(P->f64, P->n, d ? P->tptr : P->rowptr,
                                             d ? P->tidx : P->colidx, d ? P->tmap : nullptr,
                                             P->vals, L.jlev, L.ipos, L.pptr, nullptr, L.pvals,
-                                            P->num_sms * 16, s, copy_diag(P, d));
+                                            P->num_sms * 16, s, copy_diag(P, d),
+                                            d ? !P->upper : P->upper);
         if (e != cudaSuccess) return e;
     }
     for (int d = 0; d < 2; ++d) {
@@ -701,7 +703,8 @@ cudaError_t refresh_permuted(sptrsv_plan_t P, cudaStream_t s) {
         cudaError_t e = launch_permute_rows(P->f64, P->n, d ? P->tptr : P->rowptr,
                                             d ? P->tidx : P->colidx, d ? P->tmap : nullptr,
                                             P->vals, L.qord, L.qipos, L.qptr, nullptr, L.qvals,
-                                            P->num_sms * 16, s, copy_diag(P, d));
+                                            P->num_sms * 16, s, copy_diag(P, d),
+                                            d ? !P->upper : P->upper);
         if (e != cudaSuccess) return e;
     }
     // the FP32 copies of the refined solve, from the refreshed FP32 values
@@ -714,7 +717,7 @@ cudaError_t refresh_permuted(sptrsv_plan_t P, cudaStream_t s) {
                 false, P->n, d ? P->tptr : P->rowptr, d ? P->tidx : P->colidx,
                 d ? P->tmap : nullptr, P->vals32, parts ? L.qord : L.jlev,
                 parts ? L.qipos : L.ipos, parts ? L.qptr : L.pptr, nullptr, v, P->num_sms * 16, s,
-                copy_diag(P, d));
+                copy_diag(P, d), d ? !P->upper : P->upper);
             if (e != cudaSuccess) return e;
         }
     }
@@ -867,7 +870,7 @@ sptrsv_status_t build_parts(sptrsv_plan_t P, bool trans, cudaStream_t s) {
     if (e == cudaSuccess) e = launch_exclusive_scan(lens, qptr, n, s);
     if (e == cudaSuccess)
         e = launch_permute_rows(P->f64, n, ptr, idx, vmap, P->vals, qord, qipos, qptr, qidx,
-                                qvals, P->num_sms * 16, s, copy_diag(P, trans));
+                                qvals, P->num_sms * 16, s, copy_diag(P, trans), upper);
     if (e == cudaSuccess) e = launch_verify_permuted(n, qptr, qidx, P->status, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&maxpart, counters, sizeof(int),
                                               cudaMemcpyDeviceToHost, s);
@@ -921,7 +924,7 @@ sptrsv_status_t build_copy_f32(sptrsv_plan_t P, bool trans, bool parts, cudaStre
                                 trans ? P->tidx : P->colidx, trans ? P->tmap : nullptr, P->vals32,
                                 parts ? L.qord : L.jlev, parts ? L.qipos : L.ipos,
                                 parts ? L.qptr : L.pptr, nullptr, v, P->num_sms * 16, s,
-                                copy_diag(P, trans));
+                                copy_diag(P, trans), trans ? !P->upper : P->upper);
     if (e != cudaSuccess) {
         cudaFree(v);
         cudaFree(xq);
@@ -1087,6 +1090,7 @@ sptrsv_status_t run_solve(sptrsv_plan_t P, bool trans, bool f64, const void* val
         p.xp = f32_of_f64 ? L.xq32 : L.xq;
         p.prescaled = P->unit ? 0 : 1;
         p.jlev = L.qord;
+        p.diag_first = 0;  // the copy stores an upper row's entries in descending order
         p.part_ptr = L.qpart;
         p.nparts = L.qnparts;
         CK(launch_prep_self(f64, P->n, 1, p.xp, 1, nullptr, 0, nullptr, P->counters,
@@ -1110,6 +1114,7 @@ sptrsv_status_t run_solve(sptrsv_plan_t P, bool trans, bool f64, const void* val
         p.ptr = L.pptr;
         p.idx = L.pidx;
         p.vmap = nullptr;
+        p.diag_first = 0;  // the copy stores an upper row's entries in descending order
         p.vals = f32_of_f64 ? L.pvals32 : L.pvals;
         p.xp = L.xpm;
         p.prescaled = P->unit ? 0 : 1;
@@ -1133,6 +1138,7 @@ sptrsv_status_t run_solve(sptrsv_plan_t P, bool trans, bool f64, const void* val
         p.ptr = L.pptr;
         p.idx = L.pidx;
         p.vmap = nullptr;
+        p.diag_first = 0;  // the copy stores an upper row's entries in descending order
         p.vals = f32_of_f64 ? L.pvals32 : L.pvals;
         p.xp = f32_of_f64 ? L.xp32 : L.xp;
         p.prescaled = P->unit ? 0 : 1;
@@ -1522,7 +1528,7 @@ sptrsv_status_t refine_in_passes(sptrsv_plan_t P, const double* d_b, double* d_x
     r.v32 = (const float*)L.pvals32;
     r.jlev = L.jlev;
     r.unit = P->unit;
-    r.diag_first = P->upper;
+    r.diag_first = 0;  // the copy stores an upper row's entries in descending order
     r.b = d_b;
     r.ldb = ld;
     r.x = d_x;

@@ -174,7 +174,7 @@ cudaError_t launch_ordered_lengths(int n, const int* ptr, const int* jlev, int* 
 cudaError_t launch_permute_rows(bool f64, int n, const int* ptr, const int* idx, const int* vmap,
                                 const void* vals, const int* jlev, const int* ipos,
                                 const int* pptr, int* pidx, void* pvals, int grid,
-                                cudaStream_t s, int diag);
+                                cudaStream_t s, int diag, bool rev = false);
 // Self-check: every entry of row k names k or an earlier position.
 cudaError_t launch_verify_permuted(int n, const int* pptr, const int* pidx,
                                    unsigned long long* status, cudaStream_t s);

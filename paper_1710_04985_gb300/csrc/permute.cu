@@ -45,7 +45,8 @@ template <typename T>
 __global__ void permute_rows_k(int n, const int* __restrict__ ptr, const int* __restrict__ idx,
                                const int* __restrict__ vmap, const T* __restrict__ vals,
                                const int* __restrict__ jlev, const int* __restrict__ ipos,
-                               const int* __restrict__ pptr, int* pidx, T* pvals, int diag) {
+                               const int* __restrict__ pptr, int* pidx, T* pvals, int diag,
+                               int rev) {
     const int lane = threadIdx.x & 31;
     const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long k = (((long long)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5); k < n;
@@ -61,9 +62,10 @@ __global__ void permute_rows_k(int n, const int* __restrict__ ptr, const int* __
         }
         for (int e = lane; e < len; e += 32) {
             const int q = beg + e;
-            if (pidx) pidx[out + e] = ipos[idx[q]];
+            const int at = out + (rev ? len - 1 - e : e);
+            if (pidx) pidx[at] = ipos[idx[q]];
             const T v = vals[vmap ? vmap[q] : q];
-            pvals[out + e] = diag < 0 ? v : (q == qd ? dinv : v * dinv);
+            pvals[at] = diag < 0 ? v : (q == qd ? dinv : v * dinv);
         }
     }
 }
@@ -71,17 +73,17 @@ __global__ void permute_rows_k(int n, const int* __restrict__ ptr, const int* __
 cudaError_t launch_permute_rows(bool f64, int n, const int* ptr, const int* idx, const int* vmap,
                                 const void* vals, const int* jlev, const int* ipos,
                                 const int* pptr, int* pidx, void* pvals, int grid,
-                                cudaStream_t s, int diag) {
+                                cudaStream_t s, int diag, bool rev) {
     if (n <= 0) return cudaSuccess;
     long long want = ((long long)n + 7) / 8;  // 8 warps of 256 threads per block
     int g = (int)(want < grid ? want : grid);
     if (g < 1) g = 1;
     if (f64)
         permute_rows_k<double><<<g, 256, 0, s>>>(n, ptr, idx, vmap, (const double*)vals, jlev,
-                                                ipos, pptr, pidx, (double*)pvals, diag);
+                                                ipos, pptr, pidx, (double*)pvals, diag, rev);
     else
         permute_rows_k<float><<<g, 256, 0, s>>>(n, ptr, idx, vmap, (const float*)vals, jlev,
-                                               ipos, pptr, pidx, (float*)pvals, diag);
+                                               ipos, pptr, pidx, (float*)pvals, diag, rev);
     return cudaGetLastError();
 }
 

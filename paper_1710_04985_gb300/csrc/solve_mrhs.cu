@@ -60,6 +60,9 @@ __global__ void __launch_bounds__(1024) solve_mrhs_k(SolveParams p) {
     T* x = (T*)p.x;
     T* xpub = PERM ? (T*)p.xp : x;  // the array columns publish to and wait on
     const long long ldp = PERM ? p.nrhs : p.ldx;
+    // farthest dependency first: an upper row from its last entry back (the
+    // level-ordered copy already stores it that way round)
+    const bool rvs = !PERM && p.diag_first;
     int t = 0;
     if (lane == 0) t = atomicAdd(p.ticket, 1);
     t = __shfl_sync(FULL, t, 0);
@@ -105,10 +108,11 @@ __global__ void __launch_bounds__(1024) solve_mrhs_k(SolveParams p) {
                 a[e] = T(0);
                 v[e] = T(0);
                 if (q < end) {
-                    const int cc = p.idx[q];
+                    const int pq = rvs ? beg + end - 1 - q : q;  // fold order -> storage
+                    const int cc = p.idx[pq];
                     if (cc != (PERM ? self_col : i)) {
                         c[e] = cc;
-                        a[e] = vals[MAP ? p.vmap[q] : q];
+                        a[e] = vals[MAP ? p.vmap[pq] : pq];
                         live |= 1u << e;
                     }
                 }

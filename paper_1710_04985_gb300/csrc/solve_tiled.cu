@@ -53,6 +53,7 @@ __global__ void __launch_bounds__(1024) tiled_solve_k1(SolveParams p, int tile_r
     const int sl = lane - grp * W;
     const unsigned gmask = group_mask<W>(lane);
     const bool rev = p.diag_first;  // upper pattern: substitution order is n-1 .. 0
+    const bool rvs = rev;  // farthest dependency first: an upper row from its last entry back
     const T* __restrict__ vals = (const T*)p.vals;
     const T* b = (const T*)p.b;
     T* x = (T*)p.x;
@@ -100,9 +101,10 @@ __global__ void __launch_bounds__(1024) tiled_solve_k1(SolveParams p, int tile_r
                     a[e] = T(0);
                     v[e] = T(0);
                     if (q < end) {
-                        const int cc = p.idx[q];
+                        const int pq = rvs ? beg + end - 1 - q : q;  // fold order -> storage
+                        const int cc = p.idx[pq];
                         if (cc != i) {
-                            a[e] = vals[MAP ? p.vmap[q] : q];
+                            a[e] = vals[MAP ? p.vmap[pq] : pq];
                             live |= 1u << e;
                             const long long cpos =
                                 p.ipos ? (long long)p.ipos[cc]
