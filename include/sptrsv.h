@@ -404,8 +404,8 @@ SPTRSV_API sptrsv_status_t sptrsv_get_tuning(sptrsv_plan_t plan, int *lanes_per_
 /* Launch shape of multi-RHS solves (nrhs > 1, Sec. 1's many right-hand
  * sides), kept apart from the single-RHS one: a group of lanes_per_row lanes
  * in {4, 8, 16, 32} owns a row, lane l handling columns l, l + lanes_per_row,
- * ...; every column is folded in entry order, so the width does not change the
- * results.  lanes_per_row 0 (the default) picks one lane per column up to 16
+ * ...; every column is folded in the same order (farthest dependency
+ * first), so the width does not change the results.  lanes_per_row 0 (the default) picks one lane per column up to 16
  * lanes; block_size 0 and max_blocks -1 (the defaults) use the single-RHS
  * values of sptrsv_set_tuning. */
 SPTRSV_API sptrsv_status_t sptrsv_set_mrhs_tuning(sptrsv_plan_t plan, int lanes_per_row,

@@ -90,7 +90,9 @@ struct SpinPolicy {
 constexpr int kChunk = 4;
 
 // sum - a[0] v[0] - a[1] v[1] - ... over the live entries of a chunk, one FMA
-// each in entry order.  The dead slots of a chunk (the diagonal, past the
+// each in slot order (the fold order of every form: farthest dependency
+// first, so a row's diagonal, stored last in fold order, is never before a
+// live slot).  The dead slots of a chunk (the diagonal, past the
 // row's end) lie before its first live entry (the diagonal of an upper row)
 // or after its last one (the diagonal of a lower row, the row's end), and the
 // loop covers only the slots in between: a predicated-off FP64 instruction

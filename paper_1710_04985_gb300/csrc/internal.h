@@ -166,7 +166,8 @@ cudaError_t launch_row_part_keys(int n, const int* jlev, bool upper, const int* 
 // lens[k] = length of row jlev[k].
 cudaError_t launch_ordered_lengths(int n, const int* ptr, const int* jlev, int* lens,
                                    cudaStream_t s);
-// Row k of the copy = row jlev[k] in entry order: pidx = ipos[idx] (skipped
+// Row k of the copy = row jlev[k] in fold order (rev: last entry first, for
+// an upper row): pidx = ipos[idx] (skipped
 // when pidx is nullptr, a values-only refresh), pvals = vals[vmap[q] or q];
 // diag >= 0: pre-scaled by 1/d(i), with 1/d(i) in the diagonal's slot (the
 // diagonal is the first entry of a row for diag = 1, the last for 0); -1:

@@ -5,7 +5,9 @@
 // preordering the matrix by level would restore that locality.  This file
 // builds that preordering without touching the caller's arrays: position k
 // of the level order jlev (Sec. 4.1) becomes row k of a copy whose entries
-// are those of row jlev[k] in their original order, with every column index
+// are those of row jlev[k] in fold order -- a lower row's in their stored
+// order, an upper row's reversed, so that every row is folded farthest
+// dependency first (its diagonal then comes last) -- with every column index
 // j replaced by the position ipos[j] of unknown j in jlev and the value
 // copied beside it.  Dependencies then point to earlier positions (their
 // levels are lower), a warp's rows are contiguous in memory, and the
@@ -33,7 +35,8 @@ cudaError_t launch_ordered_lengths(int n, const int* ptr, const int* jlev, int* 
 }
 
 // One warp per position k; lanes stride over the row's entries, so long rows
-// are copied with coalesced loads and stores.  pidx == nullptr refreshes the
+// are copied with coalesced loads and stores; rev stores them last to first
+// (an upper row: the fold order of every form).  pidx == nullptr refreshes the
 // values only.  diag >= 0 (a matrix with a stored, used diagonal; 1: the
 // diagonal is a row's first entry, 0: its last) stores the row pre-scaled
 // as the self-scheduled kernels use it: 1/d(i) in the diagonal's slot and

@@ -3,7 +3,8 @@
 // right-hand-side columns l, l + W, ...  Each stored entry is read once per
 // column tile and applied to all of them, so the matrix traffic is shared by
 // the k solves (the multiple-right-hand-side case of Sec. 1).  No reduction
-// is needed: each lane accumulates its own column in entry order and
+// is needed: each lane accumulates its own column in fold order (farthest
+// dependency first: an upper row from its last entry back) and
 // publishes it by itself, so in the self-scheduled form every (row, column)
 // value is its own ready flag and lanes never wait for each other.
 #include "internal.h"

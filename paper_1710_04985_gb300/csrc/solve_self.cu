@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(1024) self_solve_k1(SolveParams p) {
         long long waits = 0;
         unsigned ns = 32;
         while (true) {
-            if (!lane_done && pend == 0) {  // fold a complete chunk in entry order
+            if (!lane_done && pend == 0) {  // fold a complete chunk in fold order
                 sum = fold_chunk(sum, a, v, live);
                 q0 += W * E;
                 if (q0 >= end) {
