@@ -61,9 +61,9 @@ cudaError_t launch_prep_self(bool f64, int n, int nrhs, void* x, long long ldx, 
 
 // PERM: the pattern is the plan's level-ordered copy (SPTRSV_ALGO_SELF_PERMUTED):
 // row position k of jlev holds the entries of row jlev[k] in fold order (an
-// upper row's last entry first), with column indices renumbered to positions and the values copied
-// alongside (p.ptr, p.idx, p.vals), so a warp's rows and the unknowns they
-// wait on are contiguous.  Results are published in p.xp (position order,
+// upper row's last entry first), with column indices renumbered to positions
+// and the values copied alongside (p.ptr, p.idx, p.vals), so a warp's rows and
+// the unknowns they wait on are contiguous.  Results are published in p.xp (position order,
 // the array that is polled) and stored to x(jlev[k]) for the caller.  The
 // arithmetic and its order are those of the unpermuted kernel, so both give
 // bitwise identical results for the same sub-warp width.
