@@ -323,12 +323,15 @@ def test_solve_transpose(name, algo):
             assert relerr(y, ref) <= TOL64
 
 
-def test_bitwise_determinism_and_algo_agreement():
-    """The pull form fixes each row's reduction order, so repeated solves
-    agree bit for bit.  The level-scheduled form divides by d(i) (Alg. 1)
-    and the self-scheduled one multiplies by 1/d(i) (as the paper's SLFR
-    kernel does), so the two agree to rounding."""
-    A = mat("general")
+@pytest.mark.parametrize("name", ["general", "general_upper", "ilu_U"])
+def test_bitwise_determinism_and_algo_agreement(name):
+    """The pull form fixes each row's reduction order (farthest dependency
+    first: an upper row from its last entry back, in place and in every
+    copy), so repeated solves agree bit for bit and so do the forms.  The
+    level-scheduled form divides by d(i) (Alg. 1) and the self-scheduled one
+    multiplies by 1/d(i) (as the paper's SLFR kernel does), so the two agree
+    to rounding."""
+    A = mat(name)
     with plan_for(A) as p:
         bt = torch.tensor(synth.uniform(A.n, 17), device=dev())
         first = p.solve(bt).clone()
@@ -346,15 +349,15 @@ def test_bitwise_determinism_and_algo_agreement():
                 assert torch.equal(p.solve(bt, algo="tiled"), first)
         for _ in range(3):
             assert torch.equal(p.solve(bt, algo="chains"), first)
-        # so do the level-ordered copy, whose rows keep their entry order, and
-        # the blocked solve on it (any tile size)
+        # so do the level-ordered copy, whose rows are stored in fold order,
+        # and the blocked solve on it (any tile size)
         for _ in range(3):
             assert torch.equal(p.solve(bt, algo="permuted"), first)
         for tile in (64, 1000, 4096):
             p.set_tiling(tile, False)
             assert torch.equal(p.solve(bt, algo="blocked"), first)
         # and the partitioned solve, whatever the part size
-        for rows in (0, 1, 77, 1000, 20011, 1 << 20):
+        for rows in (0, 1, 77, 1000, A.n, 1 << 20):
             p.set_partition(rows)
             assert torch.equal(p.solve(bt, algo="partitioned"), first), rows
         tg = torch.tensor(synth.uniform(A.n, 23), device=dev())
