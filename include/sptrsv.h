@@ -335,6 +335,9 @@ SPTRSV_API sptrsv_status_t sptrsv_residual(sptrsv_plan_t plan, const double *d_b
  * corrections.
  *   d_b, d_x     device FP64 [n][ld]; x is overwritten (no initial guess)
  *   iters        out (nullable): corrections applied after the first solve
+ *                (at least one when max_iter >= 1 in the staged form:
+ *                an FP32 solve alone does not meet an FP64 stop rule,
+ *                so the first correction is taken without reading the norm)
  *   rel_resid    out (nullable): the last relative residual measured
  * Synchronises `stream` once per iteration to read the residual norm; the
  * first call allocates the FP32 copy of the values, FP32 copies of the

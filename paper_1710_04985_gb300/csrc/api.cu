@@ -1638,6 +1638,16 @@ sptrsv_status_t sptrsv_solve_refined(sptrsv_plan_t plan, const double* d_b, doub
     ST(correction(true));
     int it = 0;
     double rel = 0.0;
+    if (max_iter >= 1) {
+        // An FP32 solve alone does not reach the FP64 stop rule: the first
+        // correction follows without reading the residual norm (one host
+        // round trip fewer; with b = 0 it adds a zero correction).
+        CK(launch_residual(n, P->nnz, P->rowptr, P->colidx, (const double*)P->vals, P->unit,
+                           nrhs, d_b, ld, d_x, ld, nullptr, 0, P->r32, nullptr, false, grid, s));
+        launches += 1;
+        ST(correction(false));
+        it = 1;
+    }
     for (;;) {
         // r = b - A x in FP64, its FP32 copy (the next right-hand side),
         // max|r|, max|x| and, once per set of values, ||A||_inf, in one pass
