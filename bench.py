@@ -390,7 +390,7 @@ def main():
     ku_ms, ku_n = pu.profile_read()
     pl.profile(False)
     pu.profile(False)
-    launches = args.steps * 4
+    launches = args.steps * (pl.last_launch_count + pu.last_launch_count)
     ms = max_over_ranks(ms, pg, dev)
     value = aggregate_rate(2 * args.steps, world, ms)
     bytes_solve = effective_bytes(n, nnz)

@@ -516,6 +516,51 @@ def test_partitioned_part_sizes(name):
                 p.set_partition(*bad)
 
 
+@pytest.mark.parametrize("cluster", [1, 4])
+def test_partitioned_repeated_solves_and_graph_replays(cluster):
+    """Every partitioned solve starts from a publication buffer and a ticket
+    that the previous solve left behind.  A value or a ticket carried over
+    would hand a dependent row the result of an earlier solve, or skip parts,
+    so solves with a new right-hand side each time (both directions, grids
+    smaller than the parts, and CUDA-graph replays of one captured solve)
+    must each stay within 1e-12 of the oracle, and an unchanged right-hand
+    side must give bitwise the same x."""
+    A = mat("ilu_L")
+    with plan_for(A) as p:
+        p.set_partition(240, cluster)
+        for lanes, block, grid in ((1, 128, 0), (1, 128, cluster), (4, 256, 0)):
+            p.set_tuning(lanes, block, grid)
+            first = None
+            for k in range(5):
+                b = synth.uniform(A.n, 300 + k)
+                bt = torch.tensor(b, device=dev())
+                ref = oracle.solve(A.rowptr, A.colidx, A.vals, b, upper=A.upper, unit=A.unit)
+                assert relerr(p.solve(bt, algo="partitioned"), ref) <= TOL64, (lanes, grid, k)
+                reft = oracle.solve_transpose(A.rowptr, A.colidx, A.vals, b, upper=A.upper,
+                                              unit=A.unit)
+                assert relerr(p.solve_transpose(bt, algo="partitioned"), reft) <= TOL64
+                if k == 0:
+                    b0, first = bt, p.solve(bt, algo="partitioned")
+            assert torch.equal(p.solve(b0, algo="partitioned"), first)
+        assert p.status() == (0, -1)
+        # graph replays of one captured solve, a new right-hand side each time
+        p.set_tuning(1, 128, 0)
+        bs = torch.zeros(A.n, dtype=torch.float64, device=dev())
+        xs = torch.empty_like(bs)
+        p.solve(bs, out=xs, algo="partitioned")
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            p.solve(bs, out=xs, algo="partitioned")
+        for k in range(4):
+            b = synth.uniform(A.n, 400 + k)
+            bs.copy_(torch.tensor(b, device=dev()))
+            g.replay()
+            ref = oracle.solve(A.rowptr, A.colidx, A.vals, b, upper=A.upper, unit=A.unit)
+            assert relerr(xs, ref) <= TOL64, k
+        assert p.status() == (0, -1)
+
+
 def _bad(n, rows, cols, vals, upper=False, unit=False):
     rows = np.asarray(rows)
     rowptr = np.zeros(n + 1, dtype=np.int32)
