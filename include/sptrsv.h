@@ -207,6 +207,11 @@ typedef enum {
 
 /* ------------------------------------------------------------------ setup */
 
+/* Largest matrix order and number of stored entries: 2^31 - 256.  A solve
+ * kernel's cursor over a row's entries may run up to 128 entries past the
+ * row's end and stays a 32-bit int. */
+#define SPTRSV_MAX_SIZE 2147483392
+
 /* Setup phase (Sec. 4.4, Table 1): validates the CSR (Sec. 3), builds the
  * CSR of the transpose (pattern and value map, Table 1's TRANS_GPU), computes
  * the 0-based level of every row, lev(i) = 1 + max lev(j) over the
@@ -214,7 +219,8 @@ typedef enum {
  * SPTRSV_ANALYSIS_AUTO, and the level sets (nlev, ilev[nlev+1], jlev[n])
  * with rows in ascending index order inside a level.  An upper triangle is
  * swept in reverse (Sec. 4.1).
- *   n, nnz        matrix order and stored entries (0 <= n, 0 <= nnz < 2^31)
+ *   n, nnz        matrix order and stored entries, 0 <= n, nnz <= SPTRSV_MAX_SIZE
+ *                 (SPTRSV_ERR_INVALID_ARG beyond)
  *   d_rowptr ...  device CSR, borrowed until sptrsv_free (see above)
  *   dtype         element type of d_vals
  *   uplo, diag    triangle and diagonal kind

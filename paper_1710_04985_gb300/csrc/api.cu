@@ -1250,6 +1250,10 @@ sptrsv_status_t sptrsv_analyze(int n, int nnz, const int* d_rowptr, const int* d
         (uplo != SPTRSV_LOWER && uplo != SPTRSV_UPPER) ||
         (diag != SPTRSV_NON_UNIT && diag != SPTRSV_UNIT))
         return SPTRSV_ERR_INVALID_ARG;
+    // a lane's cursor over a row's entries runs up to 32 x kChunk entries
+    // past the row's end: below SPTRSV_MAX_SIZE it stays an int
+    static_assert(32 * kChunk <= 2147483647 - SPTRSV_MAX_SIZE, "cursor headroom");
+    if (n > SPTRSV_MAX_SIZE || nnz > SPTRSV_MAX_SIZE) return SPTRSV_ERR_INVALID_ARG;
     if (n > 0 && (!d_rowptr || (nnz > 0 && (!d_colidx || !d_vals)))) return SPTRSV_ERR_INVALID_ARG;
     if (n > 0 && nnz == 0 && diag == SPTRSV_NON_UNIT) {
         g_last_error_row = 0;

@@ -312,6 +312,7 @@ extern "C" SPTRSV_API sptrsv_status_t sptrsv_solve_noalloc(
         (diag != SPTRSV_NON_UNIT && diag != SPTRSV_UNIT))
         return SPTRSV_ERR_INVALID_ARG;
     if (n > SPTRSV_NOALLOC_MAX_ROWS) return SPTRSV_ERR_INVALID_ARG;  // beyond the scratch array
+    if (nnz > SPTRSV_MAX_SIZE) return SPTRSV_ERR_INVALID_ARG;
     if (n == 0) return SPTRSV_OK;
     if (!d_rowptr || !d_b || !d_x || (nnz > 0 && (!d_colidx || !d_vals)))
         return SPTRSV_ERR_INVALID_ARG;

@@ -62,6 +62,18 @@ def test_host_argument_checks_without_gpu(lib):
     assert lib.sptrsv_analyze(0, 0, None, None, None, 7, 0, 0, None, ctypes.byref(h)) == 1
     assert lib.sptrsv_analyze(0, 0, None, None, None, 0, 3, 0, None, ctypes.byref(h)) == 1
     assert lib.sptrsv_analyze(0, 0, None, None, None, 0, 0, 2, None, None) == 1
+    # sizes past SPTRSV_MAX_SIZE (2^31 - 256): a lane's cursor over a row's
+    # entries runs up to 128 entries past the row's end and must stay an int
+    big = 2 ** 31 - 255
+    m = re.search(r"#define\s+SPTRSV_MAX_SIZE\s+(\d+)", open(HEADER).read())
+    assert m and int(m.group(1)) == big - 1
+    p8 = ctypes.c_void_p(8)
+    assert lib.sptrsv_analyze(1, big, p8, p8, p8, 0, 0, 0, None, ctypes.byref(h)) == 1
+    assert lib.sptrsv_analyze(big, 1, p8, p8, p8, 0, 0, 1, None, ctypes.byref(h)) == 1
+    assert h.value is None
+    row = ctypes.c_int(7)
+    assert lib.sptrsv_solve_noalloc(1, big, p8, p8, p8, 0, 0, 0, p8, p8, None,
+                                    ctypes.byref(row)) == 1
     # a non-unit matrix with no stored entry has a zero pivot in row 0
     assert lib.sptrsv_analyze(3, 0, ctypes.c_void_p(8), None, None, 0, 0, 0, None,
                               ctypes.byref(h)) == 3
