@@ -45,6 +45,21 @@ def _dev_int_array(ptr, n, device):
     return torch.as_tensor(_DeviceArray(ptr, n, "<i4"), device=device).clone()
 
 
+def _need(t, name: str, dtype, device, fn: str):
+    """A tensor the library reads or writes through a raw device pointer:
+    its element type and device are those the call assumes (a host tensor
+    or a narrower type would be read or written out of bounds on the GPU)."""
+    if not isinstance(t, torch.Tensor) or t.dtype != dtype or t.device != device:
+        raise ValueError(f"{fn}: {name} must be a {dtype} tensor on {device}")
+
+
+def _like(b: torch.Tensor):
+    """An output with b's shape and strides (b already checked by
+    _rhs_layout): residual and the refined solve take one leading dimension
+    for their input and output arrays."""
+    return torch.empty_strided(b.shape, b.stride(), dtype=b.dtype, device=b.device)
+
+
 def _rhs_layout(t: torch.Tensor, n: int, name: str):
     """(nrhs, ld) of a row-major [n][ld] right-hand-side tensor."""
     if t.dim() == 1:
@@ -75,6 +90,8 @@ class TriangularPlan:
         if vals.dtype not in (torch.float64, torch.float32) or not vals.is_cuda or \
                 not vals.is_contiguous():
             raise ValueError("vals must be a contiguous float64/float32 CUDA tensor")
+        if not rowptr.device == colidx.device == vals.device:
+            raise ValueError("rowptr, colidx and vals must be on one device")
         self.n = rowptr.numel() - 1
         self.nnz = colidx.numel()
         if vals.numel() != self.nnz:
@@ -144,13 +161,13 @@ class TriangularPlan:
     best_algo_mrhs = "self"   # the multi-RHS form of algo="auto" (set by the autotuner)
 
     def _solve(self, fn, name, b, out, algo, stream):
+        _need(b, "b", self.dtype, self.device, name)
+        k, ld = _rhs_layout(b, self.n, "b")
         if algo == "auto":
-            algo = self.best_algo if b.dim() == 1 or b.shape[1] == 1 else self.best_algo_mrhs
-        if b.dtype != self.dtype or b.device != self.device:
-            raise ValueError(f"{name}: b must be {self.dtype} on {self.device}")
+            algo = self.best_algo if k == 1 else self.best_algo_mrhs
         if out is None:
             out = torch.empty_like(b, memory_format=torch.contiguous_format)
-        k, ld = _rhs_layout(b, self.n, "b")
+        _need(out, "out", self.dtype, self.device, name)
         k2, ld2 = _rhs_layout(out, self.n, "out")
         if k2 != k or ld2 != ld:
             raise ValueError(f"{name}: out must have the layout of b")
@@ -190,21 +207,33 @@ class TriangularPlan:
 
     def grad_vals(self, y, x, out=None, stream=None):
         """-y_i . x_j on every stored (i, j): dloss/dA given y = A^{-T} dloss/dx."""
+        _need(x, "x", self.dtype, self.device, "grad_vals")
+        _need(y, "y", self.dtype, self.device, "grad_vals")
         k, ld = _rhs_layout(x, self.n, "x")
         ky, ldy = _rhs_layout(y, self.n, "y")
         if (k, ld) != (ky, ldy):
             raise ValueError("grad_vals: x and y must share their layout")
         if out is None:
             out = torch.empty(self.nnz, dtype=self.dtype, device=self.device)
+        _need(out, "out", self.dtype, self.device, "grad_vals")
+        if out.numel() != self.nnz or not out.is_contiguous():
+            raise ValueError(f"grad_vals: out must be a contiguous vector of length {self.nnz}")
         check(_lib.load().sptrsv_grad_vals(self._h, _ptr(y), _ptr(x), k, ld, _ptr(out),
                                            _stream_handle(stream)), "sptrsv_grad_vals")
         return out
 
     def residual(self, b, x, out=None, stream=None):
         """r = b - A x in FP64."""
-        k, ld = _rhs_layout(b, self.n, "b")
+        for name, t in (("b", b), ("x", x)):
+            _need(t, name, torch.float64, self.device, "residual")
+        k, ld = _rhs_layout(b, self.n, "b")  # before _like(b): b's strides are valid
+        if _rhs_layout(x, self.n, "x") != (k, ld):
+            raise ValueError("residual: x must have the layout of b")
         if out is None:
-            out = torch.empty_like(b)
+            out = _like(b)
+        _need(out, "out", torch.float64, self.device, "residual")
+        if _rhs_layout(out, self.n, "out") != (k, ld):
+            raise ValueError("residual: out must have the layout of b")
         check(_lib.load().sptrsv_residual(self._h, _ptr(b), _ptr(x), _ptr(out), k, ld,
                                           _stream_handle(stream)), "sptrsv_residual")
         return out
@@ -213,9 +242,13 @@ class TriangularPlan:
         """FP32 bulk solves + FP64 residual/update iterative refinement.
 
         Returns ``(x, iterations, relative_residual)``."""
-        k, ld = _rhs_layout(b, self.n, "b")
+        _need(b, "b", torch.float64, self.device, "solve_refined")
+        k, ld = _rhs_layout(b, self.n, "b")  # before _like(b): b's strides are valid
         if out is None:
-            out = torch.empty_like(b)
+            out = _like(b)
+        _need(out, "out", torch.float64, self.device, "solve_refined")
+        if _rhs_layout(out, self.n, "out") != (k, ld):
+            raise ValueError("solve_refined: out must have the layout of b")
         it = ctypes.c_int(0)
         rel = ctypes.c_double(0.0)
         check(_lib.load().sptrsv_solve_refined(self._h, _ptr(b), _ptr(out), k, ld, max_iter,
@@ -241,8 +274,9 @@ class TriangularPlan:
               "sptrsv_set_refine_mode")
 
     def set_values(self, vals, stream=None):
-        if vals.dtype != self.dtype or vals.numel() != self.nnz or not vals.is_contiguous():
-            raise ValueError("set_values: same dtype and length, contiguous")
+        if vals.dtype != self.dtype or vals.device != self.device or \
+                vals.numel() != self.nnz or not vals.is_contiguous():
+            raise ValueError("set_values: same dtype, device and length, contiguous")
         check(_lib.load().sptrsv_set_values(self._h, _ptr(vals), _stream_handle(stream)),
               "sptrsv_set_values")
         self._keep[2] = vals
