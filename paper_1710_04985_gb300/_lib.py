@@ -77,6 +77,7 @@ SIGNATURES = [
 ]
 
 NOALLOC_MAX_ROWS = 4194304
+MAX_SIZE = 2147483392   # SPTRSV_MAX_SIZE: largest n and nnz a plan accepts (2^31 - 256)
 
 _lib = None
 

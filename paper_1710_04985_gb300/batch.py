@@ -17,7 +17,7 @@ from __future__ import annotations
 
 import torch
 
-from . import autotune
+from . import _lib, autotune
 from .solver import TriangularPlan
 
 
@@ -26,20 +26,27 @@ def block_diagonal(systems, device="cuda", dtype=torch.float64):
     block-diagonal CSR on `device`.  Returns (rowptr, colidx, vals, offsets)
     with ``offsets[s]`` the first row of system s."""
     rps, cis, vas, sizes, nnzs = [], [], [], [], []
-    for rp, ci, va in systems:
+    for s, (rp, ci, va) in enumerate(systems):
         rp = torch.as_tensor(rp).to(device=device, dtype=torch.int64)
         rps.append(rp)
         cis.append(torch.as_tensor(ci).to(device=device, dtype=torch.int64))
         vas.append(torch.as_tensor(va).to(device=device, dtype=dtype))
+        if rp.dim() != 1 or rp.numel() < 1:
+            raise ValueError(f"system {s}: rowptr must be a vector of n + 1 entries")
         sizes.append(rp.numel() - 1)
         nnzs.append(int(rp[-1].item()))
+        # the offsets below shift every system by the entries of the ones before
+        if int(rp[0].item()) != 0 or nnzs[-1] != cis[-1].numel() or \
+                cis[-1].numel() != vas[-1].numel():
+            raise ValueError(f"system {s}: rowptr must run from 0 to the number of entries, "
+                             "and colidx and vals must hold that many")
     offsets = [0]
     nnz_off = [0]
     for nk, zk in zip(sizes, nnzs):
         offsets.append(offsets[-1] + nk)
         nnz_off.append(nnz_off[-1] + zk)
-    if offsets[-1] >= 2 ** 31 or nnz_off[-1] >= 2 ** 31:
-        raise ValueError("batch too large for int32 indices")
+    if offsets[-1] > _lib.MAX_SIZE or nnz_off[-1] > _lib.MAX_SIZE:
+        raise ValueError("batch larger than the solver's index range (SPTRSV_MAX_SIZE)")
     rowptr = torch.cat([rp[:-1] + nnz_off[s] for s, rp in enumerate(rps)] +
                        [torch.tensor([nnz_off[-1]], device=device, dtype=torch.int64)])
     colidx = torch.cat([ci + offsets[s] for s, ci in enumerate(cis)])

@@ -67,6 +67,8 @@ def test_host_argument_checks_without_gpu(lib):
     big = 2 ** 31 - 255
     m = re.search(r"#define\s+SPTRSV_MAX_SIZE\s+(\d+)", open(HEADER).read())
     assert m and int(m.group(1)) == big - 1
+    from paper_1710_04985_gb300 import _lib
+    assert _lib.MAX_SIZE == big - 1
     p8 = ctypes.c_void_p(8)
     assert lib.sptrsv_analyze(1, big, p8, p8, p8, 0, 0, 0, None, ctypes.byref(h)) == 1
     assert lib.sptrsv_analyze(big, 1, p8, p8, p8, 0, 0, 1, None, ctypes.byref(h)) == 1

@@ -85,3 +85,18 @@ def test_plan_refuses_host_or_mixed_device_arrays():
     v = torch.ones(1, dtype=torch.float64)
     with pytest.raises(ValueError):
         TriangularPlan(rp, ci, v)            # host tensors
+
+
+def test_block_diagonal_concatenates_and_refuses_inconsistent_systems():
+    from paper_1710_04985_gb300.batch import block_diagonal
+    sys0 = ([0, 1, 3], [0, 0, 1], [2.0, 1.0, 3.0])           # 2 x 2 lower
+    sys1 = ([0, 1], [0], [5.0])                               # 1 x 1
+    rp, ci, va, off = block_diagonal([sys0, sys1], device="cpu")
+    assert rp.tolist() == [0, 1, 3, 4] and rp.dtype == torch.int32
+    assert ci.tolist() == [0, 0, 1, 2] and ci.dtype == torch.int32
+    assert va.tolist() == [2.0, 1.0, 3.0, 5.0] and off == [0, 2, 3]
+    for bad in (([0, 1, 2], [0, 0, 1], [2.0, 1.0, 3.0]),     # rowptr ends short of colidx
+                ([0, 1, 3], [0, 0, 1], [2.0, 1.0]),          # fewer values than entries
+                ([1, 2, 4], [0, 0, 1], [2.0, 1.0, 3.0])):    # rowptr not from 0
+        with pytest.raises(ValueError):
+            block_diagonal([sys1, bad], device="cpu")
