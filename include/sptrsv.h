@@ -286,8 +286,9 @@ SPTRSV_API sptrsv_status_t sptrsv_solve_transpose(sptrsv_plan_t plan, const void
                                        void *d_x, int nrhs, int ld,
                                        sptrsv_algo_t algo, void *stream);
 
-/* Builds the transposed pattern and its levels now (see
- * sptrsv_solve_transpose); synchronises `stream`. */
+/* Builds the transposed pattern (the CSC view of Sec. 3.2) and its levels
+ * (Sec. 4.1, swept in the opposite direction) now, as the first
+ * sptrsv_solve_transpose would; synchronises `stream`. */
 SPTRSV_API sptrsv_status_t sptrsv_prepare_transpose(sptrsv_plan_t plan, void *stream);
 
 /* Builds now whatever the first solve of `algo` (SPTRSV_ALGO_AUTO: the
@@ -316,8 +317,8 @@ SPTRSV_API sptrsv_status_t sptrsv_grad_vals(sptrsv_plan_t plan, const void *d_y,
 
 /* --------------------------------------------------------------- precision */
 
-/* FP64 residual r = b - A x of system (1) (diagonal taken as 1 for a unit
- * plan).  F64 plans only.  All three arrays [n][ld], device.  Asynchronous. */
+/* FP64 residual r = b - A x of system (1), eq. (1) (diagonal taken as 1 for
+ * a unit plan).  F64 plans only.  All three arrays [n][ld], device.  Asynchronous. */
 SPTRSV_API sptrsv_status_t sptrsv_residual(sptrsv_plan_t plan, const double *d_b,
                                 const double *d_x, double *d_r, int nrhs,
                                 int ld, void *stream);
@@ -481,16 +482,17 @@ SPTRSV_API sptrsv_status_t sptrsv_set_spin_limit(sptrsv_plan_t plan, long long p
 
 /* -------------------------------------------------------------- inspection */
 
-/* Level data of the forward (transpose = 0) or transposed (transpose = 1)
- * system: nlev, and device pointers (owned by the plan) to lev[n],
- * ilev[nlev+1] and jlev[n].  The transposed data exist only after
+/* Level data (Sec. 4.1) of the forward (transpose = 0) or transposed
+ * (transpose = 1) system: nlev, and device pointers (owned by the plan) to
+ * lev[n], ilev[nlev+1] and jlev[n].  The transposed data exist only after
  * sptrsv_prepare_transpose or a transposed solve. */
 SPTRSV_API sptrsv_status_t sptrsv_levels(sptrsv_plan_t plan, int transpose, int *nlev,
                               const int **d_lev, const int **d_ilev,
                               const int **d_jlev);
 
-/* Transposed pattern (CSR of A^T): tptr[n+1], tidx[nnz] and tmap[nnz], with
- * (A^T) entry q equal to d_vals[tmap[q]]. */
+/* Transposed pattern (CSR of A^T, the CSC view of Sec. 3.2): tptr[n+1],
+ * tidx[nnz] and tmap[nnz], device pointers owned by the plan, with (A^T)
+ * entry q equal to d_vals[tmap[q]]. */
 SPTRSV_API sptrsv_status_t sptrsv_transpose_pattern(sptrsv_plan_t plan,
                                          const int **d_tptr,
                                          const int **d_tidx,
@@ -550,8 +552,9 @@ SPTRSV_API int sptrsv_last_launch_count(sptrsv_plan_t plan);
  * plan either, since the analysis allocates its level sets.
  *
  * What it does, all enqueued on `stream`: clears its working memory,
- * validates the CSR as sptrsv_analyze does, then runs a self-scheduled solve
- * in substitution order (rows wait for per-row ready flags; no level sets).
+ * validates the CSR as sptrsv_analyze does, then runs the self-scheduled
+ * solve of Alg. 3 with rows handed out in substitution order instead of
+ * level order (rows wait for per-row ready flags; no level sets).
  *   n, nnz, d_rowptr, d_colidx, d_vals, dtype, uplo, diag: as sptrsv_analyze
  *   d_b, d_x   device vectors of n elements, contiguous; d_x == d_b allowed
  *   error_row  NULL: return right after enqueueing; SPTRSV_OK then only
@@ -563,7 +566,8 @@ SPTRSV_API int sptrsv_last_launch_count(sptrsv_plan_t plan);
  * A dependency wait gives up after SPTRSV_SPIN_LIMIT polls (environment
  * variable, read at every call; 2^24 by default), reports
  * SPTRSV_ERR_TIMEOUT for its row and goes on with NaN.
- * Returns SPTRSV_ERR_INVALID_ARG for n > SPTRSV_NOALLOC_MAX_ROWS.
+ * Returns SPTRSV_ERR_INVALID_ARG for n > SPTRSV_NOALLOC_MAX_ROWS or
+ * nnz > SPTRSV_MAX_SIZE.
  * Working memory: one array declared at file scope in the library, shared by
  * every call; each call clears the parts it uses before reading them, and
  * the array keeps the last call's contents afterwards.  Calls whose GPU work

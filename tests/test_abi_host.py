@@ -120,3 +120,18 @@ def test_oracle_and_cuda_path_share_no_code():
                          capture_output=True, text=True, check=True).stdout
     syms = {ln.split()[-1] for ln in out.splitlines() if " T " in ln}
     assert syms and all(s.startswith("oracle_") for s in syms)
+
+
+def test_operation_entry_points_cite_the_passage_they_implement():
+    """Every call that computes something names the part of the paper that
+    defines it (section, algorithm, equation or table) in its comment."""
+    text = open(HEADER).read()
+    comments = {m.group(2): m.group(1) for m in re.finditer(
+        r"/\*((?:(?!\*/).)*)\*/\s*SPTRSV_API[^;]*?\b(sptrsv_\w+)\s*\(", text, re.S)}
+    ops = ("sptrsv_analyze", "sptrsv_reanalyze", "sptrsv_solve", "sptrsv_solve_transpose",
+           "sptrsv_prepare_transpose", "sptrsv_prepare", "sptrsv_grad_vals", "sptrsv_residual",
+           "sptrsv_solve_refined", "sptrsv_levels", "sptrsv_transpose_pattern",
+           "sptrsv_partition_info", "sptrsv_solve_noalloc")
+    for name in ops:
+        assert name in comments, name
+        assert re.search(r"\b(Sec\.|Alg\.|eq\.|Table)", comments[name]), name
